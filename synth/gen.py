@@ -1,0 +1,110 @@
+"""Counter-based SplitMix64 residues and the workload shapes (no RowSel arithmetic)."""
+
+import numpy as np
+
+GAMMA = 0x9E3779B97F4A7C15
+TAGMUL = 0xD1B54A32D192ED03
+M1 = 0xBF58476D1CE4E5B9
+M2 = 0x94D049BB133111EB
+MASK64 = (1 << 64) - 1
+
+TAG_DB = 1        # database residues
+TAG_CT = 2        # selection-ciphertext residues
+TAG_SECRET = 3    # toy RLWE secret
+TAG_MASK = 4      # toy RLWE uniform "a" polynomials
+
+# The two largest primes below 2^28 that are 1 mod 8192 (so NTT-friendly for
+# every N <= 4096): 0xFFF0001 and 0xFFEE001.
+PRIMES_28 = (268369921, 268361729)
+
+
+def mix64(z: int) -> int:
+    z &= MASK64
+    z = ((z ^ (z >> 30)) * M1) & MASK64
+    z = ((z ^ (z >> 27)) * M2) & MASK64
+    return z ^ (z >> 31)
+
+
+def stream_key(seed: int, tag: int) -> int:
+    return mix64(((seed * GAMMA) ^ ((tag + 1) * TAGMUL)) & MASK64)
+
+
+def _mix64_np(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(M1)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(M2)
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform_u64(seed: int, tag: int, start: int, count: int) -> np.ndarray:
+    """value(i) for i in [start, start + count), as uint64."""
+    key = np.uint64(stream_key(seed, tag))
+    idx = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64_np(key + idx * np.uint64(GAMMA))
+
+
+def uniform_residues(seed: int, tag: int, shape, primes, limb_axis: int,
+                     chunk: int = 1 << 24) -> np.ndarray:
+    """uint32 array of `shape`; element at flat index f is value(f) mod q_l,
+    l the element's index along `limb_axis`."""
+    shape = tuple(int(s) for s in shape)
+    total = int(np.prod(shape)) if shape else 1
+    out = np.empty(total, dtype=np.uint32)
+    # limb of each flat index: (f // inner) % L
+    L = shape[limb_axis]
+    inner = int(np.prod(shape[limb_axis + 1:])) if limb_axis + 1 < len(shape) else 1
+    qs = np.asarray(primes, dtype=np.uint64)
+    if len(qs) != L:
+        raise ValueError("one prime per limb")
+    for s in range(0, total, chunk):
+        n = min(chunk, total - s)
+        v = uniform_u64(seed, tag, s, n)
+        limb = (np.arange(s, s + n, dtype=np.int64) // inner) % L
+        out[s:s + n] = (v % qs[limb]).astype(np.uint32)
+    return out.reshape(shape)
+
+
+def ct_tensor(seed: int, B: int, D0: int, L: int, N: int, primes) -> np.ndarray:
+    """Selection ciphertexts [B][D0][2][L][N], uniform residues."""
+    return uniform_residues(seed, TAG_CT, (B, D0, 2, L, N), primes, limb_axis=3)
+
+
+def db_tensor(seed: int, D0: int, D1: int, L: int, N: int, primes) -> np.ndarray:
+    """NTT-form database [D0][D1][L][N], uniform residues."""
+    return uniform_residues(seed, TAG_DB, (D0, D1, L, N), primes, limb_axis=2)
+
+
+def toy_rlwe_selection(seed: int, D0: int, L: int, N: int, primes, istar: int):
+    """Noiseless toy RLWE one-hot query in the NTT domain, for serving checks.
+
+    ct_i = (a_i, a_i (.) s + [i == istar] * 1) mod q, with a_i and s uniform.
+    (The NTT of the constant polynomial 1 is the all-ones vector.)
+    Returns (ct [D0][2][L][N] uint32, s [L][N] uint32).
+    This is query encoding on the client side, not RowSel.
+    """
+    s = uniform_residues(seed, TAG_SECRET, (L, N), primes, limb_axis=0).astype(np.uint64)
+    a = uniform_residues(seed, TAG_MASK, (D0, L, N), primes, limb_axis=1).astype(np.uint64)
+    ct = np.empty((D0, 2, L, N), dtype=np.uint32)
+    for l in range(L):
+        q = np.uint64(primes[l])
+        b = (a[:, l, :] * s[l][None, :]) % q
+        b[istar] = (b[istar] + np.uint64(1)) % q
+        ct[:, 0, l, :] = a[:, l, :].astype(np.uint32)
+        ct[:, 1, l, :] = b.astype(np.uint32)
+    return ct, s.astype(np.uint32)
+
+
+# Workloads of the GPIR RowSel study on one GB300 (synthetic, uniform residues).
+CONFIGS = {
+    "c1_plain": dict(N=2048, L=1, D0=16, D1=16, B=1, seed=0),
+    "c2_rowsel": dict(N=4096, L=2, D0=256, D1=64, B=32, seed=1),
+    "c3_sweep": dict(N=4096, L=2, D0=256, D1=64, B=(1, 8, 32, 128, 256), seed=2),
+    "c4_large": dict(N=4096, L=2, D0=1024, D1=128, B=128, seed=3),
+    "c5_serving": dict(N=4096, L=2, dbs=((256, 64), (512, 64), (1024, 128)), seed=4),
+}
+
+
+def config_shapes(name: str):
+    c = dict(CONFIGS[name])
+    c["primes"] = PRIMES_28[:c["L"]]
+    return c
