@@ -1,0 +1,427 @@
+"""RowSel benchmark on GB300: queries/s vs batch, DB GB/s, per-path comparison.
+
+One step = one batched RowSel (all of its work: every limb, slot, client and
+column) over device-resident synthetic inputs through the C ABI
+(gpir_rowsel_batch). Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--path auto|cudacore|imma|tc] [--impl gpir|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(RowSel needs no exchange between replicas); value = all ranks' queries / the
+slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from paper_2604_04696_gb300 import sizes  # noqa: E402
+
+METRIC = "RowSel queries/s vs batch; DB GB/s; INT8-TC path vs plain path, bit-exact"
+PATH_IDS = {"auto": 0, "cudacore": 1, "imma": 2, "tc": 4}
+PATH_NAMES = {1: "cudacore", 2: "imma", 4: "tc"}
+# Integer multiply-add lanes per SM (IMAD.WIDE.U32 issues at the full IMAD rate,
+# measured 17.7e12/s on 152 SMs) and the recipe's maximum SM clock.
+IMAD_PER_SM_CLK = 64
+SM_MAX_MHZ = 2070.0
+N_SMS = 152
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def workload_shape(name, batch=None):
+    c = synth.config_shapes(name)
+    B = batch if batch is not None else c["B"]
+    if not isinstance(B, int):
+        B = 32
+    return dict(N=c["N"], L=c["L"], D0=c["D0"], D1=c["D1"], B=B, seed=c["seed"], primes=list(c["primes"]))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def time_oracle_sample(w, n_slots, seed=99):
+    import oracle
+    rng = np.random.default_rng(seed)
+    slots = [(int(rng.integers(0, w["L"])), int(rng.integers(0, w["N"]))) for _ in range(n_slots)]
+    ct = synth.ct_slots(w["seed"], w["B"], w["D0"], w["L"], w["N"], w["primes"], slots)
+    db = synth.db_slots(w["seed"], w["D0"], w["D1"], w["L"], w["N"], w["primes"], slots)
+    t0 = time.perf_counter()
+    for k, (l, _t) in enumerate(slots):
+        oracle.rowsel(ct[:, :, :, None, k:k + 1], db[:, :, None, k:k + 1], [w["primes"][l]])
+    return time.perf_counter() - t0
+
+
+def oracle_queries_per_s(w, seconds_target=10.0):
+    """Time the oracle on a bounded sample of slots, extrapolate to the whole
+    batch (every limb and slot), return (queries/s, sample description)."""
+    t1 = time_oracle_sample(w, 1)
+    n = int(max(1, min(w["L"] * w["N"], seconds_target / max(t1, 1e-6))))
+    dt = time_oracle_sample(w, n, seed=7)
+    full = dt * (w["L"] * w["N"]) / n
+    return w["B"] / full, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload_shape(args.workload, args.batch)
+    total_slots = w["L"] * w["N"]
+    # per step: a slot sample sized so warm-up + steps stay within ~2 minutes
+    t1 = time_oracle_sample(w, 1)
+    per_step_budget = 100.0 / max(1, args.steps + args.warmup)
+    n = int(max(1, min(total_slots, per_step_budget / max(t1, 1e-6))))
+    for _ in range(args.warmup):
+        time_oracle_sample(w, n, seed=1)
+    times = []
+    for s in range(args.steps):
+        times.append(time_oracle_sample(w, n, seed=100 + s))
+    step = statistics.mean(times)
+    qps = w["B"] / (step * total_slots / n)
+    sample = "%d of %d (limb, slot) points per step, extrapolated to the whole batch" % (n, total_slots)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3 * total_slots / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (numpy)",
+        "data": "synthetic", "config": cfg_dict(args.workload, w, "oracle", None),
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cfg_dict(workload, w, path_name, variant):
+    alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    return {"workload": workload, "N": w["N"], "limbs": w["L"], "D0": w["D0"], "D1": w["D1"],
+            "batch": w["B"], "primes": w["primes"], "path": path_name, "variant": variant,
+            "db_bytes": sizes.db_bytes(w["D0"], w["D1"], w["N"], w["L"]),
+            "l2": "inputs larger than L2 (%.2f GB moved per step vs 129 MB L2); no flush" % (alg / 1e9)}
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_src_hash(path_id):
+    f = {1: "rowsel_cc.cu", 2: "rowsel_imma.cu", 4: "rowsel_tc.cu"}[path_id]
+    with open(os.path.join(ROOT, "paper_2604_04696_gb300", "csrc", f), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(path_id, workload, batch):
+    """DRAM bytes per launch from a committed ncu capture, or None when absent or
+    when the kernel source changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    e = t.get("%s/%s/B%d" % (PATH_NAMES[path_id], workload, batch))
+    if not e or e.get("src_sha") != kernel_src_hash(path_id):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def roofline(path_id, w, ms, peaks, workload):
+    alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    s = ms / 1e3
+    t_hbm = alg / (peaks["hbm_gbs"] * 1e9)
+    traffic = recorded_traffic(path_id, workload, w["B"])
+    if path_id == 4:
+        flops = 2.0 * 16 * macs       # 16 exact bf16 digit products per modular MAC
+        t_c = flops / (peaks["bf16_tflops"] * 1e12)
+        if t_c >= t_hbm:
+            a = flops / s / 1e12
+            return {"bound": "tensor", "achieved": a, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": a / peaks["bf16_tflops"], "traffic": traffic,
+                    "note": "bf16 digit-product flops (16 per modular MAC) vs %s cuBLAS bf16 burst" % peaks["source"]}
+    elif path_id == 2:
+        ops = 2.0 * 16 * macs         # 16 u8 x u8 products per modular MAC
+        imma_peak = 151.0             # TOPS, measured mma.sync m16n8k32 u8 on this GB300 pool
+        t_c = ops / (imma_peak * 1e12)
+        if t_c >= t_hbm:
+            a = ops / s / 1e12
+            return {"bound": "tensor", "achieved": a, "peak": imma_peak, "unit": "TOPS",
+                    "frac": a / imma_peak, "traffic": traffic,
+                    "note": "u8 products (16 per modular MAC) vs measured mma.sync IMMA peak"}
+    else:
+        alu_peak = N_SMS * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6
+        t_c = macs / alu_peak
+        if t_c >= t_hbm:
+            a = macs / s / 1e12
+            return {"bound": "alu", "achieved": a, "peak": alu_peak / 1e12, "unit": "T IMAD.WIDE/s",
+                    "frac": a * 1e12 / alu_peak, "traffic": traffic,
+                    "note": "one IMAD.WIDE.U32 per modular MAC; peak = 152 SMs x 64 lanes x 2070 MHz"}
+    a = alg / s / 1e9
+    return {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+            "traffic": traffic, "note": "algorithmic bytes (DB + cts read once, outputs written once) vs %s copy BW"
+            % peaks["source"]}
+
+
+class GpuWorkload:
+    def __init__(self, g, torch, w, path_mask):
+        self.g, self.torch, self.w = g, torch, w
+        N, L, D0, D1, B = w["N"], w["L"], w["D0"], w["D1"], w["B"]
+        self.params = g.gpir_params_create(N, w["primes"])
+        self.stream = torch.cuda.current_stream()
+        db = torch.empty(D0 * D1 * L * N, dtype=torch.int32, device="cuda")
+        g.gpir_fill_uniform(db, db.numel(), 0, w["seed"], synth.TAG_DB, self.params, N, self.stream)
+        self.h = g.gpir_db_upload(self.params, D0, D1, db, True, path_mask, self.stream)
+        del db
+        self.ct = torch.empty(B * D0 * 2 * L * N, dtype=torch.int32, device="cuda")
+        g.gpir_fill_uniform(self.ct, self.ct.numel(), 0, w["seed"], synth.TAG_CT, self.params, N, self.stream)
+        self.out = torch.empty(B * D1 * 2 * L * N, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+
+    def step(self, path):
+        self.g.gpir_rowsel_batch(self.h, self.w["B"], self.ct, self.out, path, self.stream)
+
+    def time_steps(self, path, steps, warmup, barrier=None, clocks=None):
+        torch = self.torch
+        for _ in range(warmup):
+            self.step(path)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            self.step(path)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+        clk = clocks.stop() if clocks else None
+        self.g.gpir_sync(self.stream, 60000)
+        return e0.elapsed_time(e1) / steps, clk
+
+    def check_sample(self, n_slots=3):
+        """Bit-exact check of a few sampled (limb, slot) points against the oracle."""
+        import oracle
+        w = self.w
+        rng = np.random.default_rng(5)
+        slots = [(int(rng.integers(0, w["L"])), int(rng.integers(0, w["N"]))) for _ in range(n_slots)]
+        ct = synth.ct_slots(w["seed"], w["B"], w["D0"], w["L"], w["N"], w["primes"], slots)
+        db = synth.db_slots(w["seed"], w["D0"], w["D1"], w["L"], w["N"], w["primes"], slots)
+        out = self.out.view(w["B"], w["D1"], 2, w["L"], w["N"])
+        for k, (l, t) in enumerate(slots):
+            want = oracle.rowsel(ct[:, :, :, None, k:k + 1], db[:, :, None, k:k + 1], [w["primes"][l]])[..., 0, 0]
+            got = out[:, :, :, l, t].contiguous().cpu().numpy().view(np.uint32)
+            if not np.array_equal(got, want):
+                return False
+        return True
+
+    def e2e(self, path, steps, warmup):
+        """Same metric through gpir_rowsel_batch_host: pinned host ct in, host out back,
+        copies inside the timed region."""
+        torch, g, w = self.torch, self.g, self.w
+        ct_h = torch.empty(self.ct.numel(), dtype=torch.int32, pin_memory=True)
+        ct_h.copy_(self.ct)
+        out_h = torch.empty(self.out.numel(), dtype=torch.int32, pin_memory=True)
+        for _ in range(warmup):
+            g.gpir_rowsel_batch_host(self.h, w["B"], ct_h, out_h, path, self.stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            g.gpir_rowsel_batch_host(self.h, w["B"], ct_h, out_h, path, self.stream)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return ms, ct_h.numel() * 4, out_h.numel() * 4
+
+    def close(self):
+        self.g.gpir_db_free(self.h)
+        self.g.gpir_params_destroy(self.params)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpir", choices=["gpir", "reference"])
+    ap.add_argument("--workload", default="c2_rowsel", choices=["c1_plain", "c2_rowsel", "c4_large", "c3_sweep"])
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--path", default="auto", choices=list(PATH_IDS))
+    ap.add_argument("--no-extras", action="store_true", help="skip path comparison, sweep and cpu baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    barrier = None
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = lambda: dist.barrier(device_ids=[local])
+
+    from paper_2604_04696_gb300 import _build
+    _build.build()
+    from paper_2604_04696_gb300 import gpir as g
+
+    peaks = load_peaks()
+    w = workload_shape(args.workload, args.batch)
+    built = [p for p in (1, 2, 4) if g.gpir_num_variants(p) > 0]
+    mask = 0
+    for p in built:
+        mask |= p
+    wl = GpuWorkload(g, torch, w, mask)
+
+    # choose the path: requested, else the fastest built path after autotuning each
+    per_path = {}
+    for p in built:
+        v = g.gpir_autotune(wl.h, w["B"], wl.ct, wl.out, p, wl.stream)
+        ms, _ = wl.time_steps(p, max(3, min(args.steps, 10)), 2)
+        per_path[p] = {"variant": v, "ms": ms}
+    if args.path != "auto":
+        path = PATH_IDS[args.path]
+    else:
+        path = min(per_path, key=lambda p: per_path[p]["ms"])
+    variant = per_path[path]["variant"]
+
+    clocks = Clocks(local)
+    ms, clk = wl.time_steps(path, args.steps, args.warmup, barrier=barrier, clocks=clocks)
+    exact = wl.check_sample() if rank == 0 else None
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    qps = world * w["B"] / (ms / 1e3)
+    e2e_ms, h2d, d2h = wl.e2e(path, max(3, args.steps // 2), 2)
+    e2e_val = w["B"] / (e2e_ms / 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * w["B"] / (float(t.item()) / 1e3)
+
+    db_bytes = sizes.db_bytes(w["D0"], w["D1"], w["N"], w["L"])
+    alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    line = {
+        "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {1: "u32 (u64 accumulate)", 2: "u8 (s32 accumulate)",
+                                       4: "bf16 digits (fp32 exact accumulate)"}[path],
+        "data": "synthetic", "config": cfg_dict(args.workload, w, PATH_NAMES[path], variant),
+        "db_gbs": db_bytes / (ms / 1e3) / 1e9, "alg_gbs": alg / (ms / 1e3) / 1e9,
+        "bit_exact_sample": exact,
+        "roofline": roofline(path, w, ms, peaks, args.workload),
+        "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "paths": {PATH_NAMES[p]: {"ms": v["ms"], "queries_s": w["B"] / (v["ms"] / 1e3), "variant": v["variant"]}
+                  for p, v in per_path.items()},
+    }
+    wl.close()
+    if not args.no_extras and rank == 0:
+        # queries/s vs batch on the same DB shape (best path), one line item per batch
+        if args.workload in ("c2_rowsel", "c3_sweep"):
+            sweep = []
+            for b in (1, 8, 32, 128, 256):
+                ws = workload_shape("c3_sweep", b)
+                wk = GpuWorkload(g, torch, ws, mask)
+                g.gpir_autotune(wk.h, b, wk.ct, wk.out, path, wk.stream)
+                mss, _ = wk.time_steps(path, 10, 3)
+                sweep.append({"batch": b, "ms": mss, "queries_s": b / (mss / 1e3),
+                              "roofline_frac": roofline(path, ws, mss, peaks, "c3_sweep")["frac"]})
+                wk.close()
+            line["sweep"] = sweep
+        if world == 1:
+            v, n, dt = oracle_queries_per_s(w, seconds_target=10.0)
+            line["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                                    "sample": "%d of %d (limb, slot) points in %.1f s, extrapolated"
+                                              % (n, w["L"] * w["N"], dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

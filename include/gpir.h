@@ -1,0 +1,168 @@
+/*
+ * gpir.h -- C ABI of the GB300 RowSel library (libgpir.so).
+ *
+ * RowSel is the encrypted row-selection step of batched lattice PIR as the
+ * GPIR paper (arXiv 2604.04696) defines it: each client's D0 NTT-domain RLWE
+ * selection ciphertexts are multiplied point-wise with the D0 x D1 NTT-form
+ * plaintext database and summed over the rows (Sec. 2.2, "RowSel"). Written
+ * per NTT point p this is the GEMM of Sec. 2.3,
+ *     M_out[p, m, n] = sum_k M_in0[p, m, k] * M_in1[p, k, n]   (mod q_l),
+ * with m = (client, polynomial) of extent 2*batch (Sec. 5.1.1), k the D0 rows,
+ * n the D1 columns, and p = (limb l, slot t) over L RNS limbs of N slots
+ * (Sec. 2.4.1: "4N points" for four limbs).
+ *
+ * Conventions for every call:
+ *  - Residues are canonical uint32 values in [0, q_l).
+ *  - Device pointers are CUDA device addresses of the current device; host
+ *    pointers are ordinary (preferably pinned) host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls that take a stream are asynchronous on it unless stated otherwise.
+ *  - The caller owns ciphertext and output buffers; the library owns the
+ *    params object, its device copy of each database and any workspace.
+ *  - Every call returns GPIR_OK (0) or a negative gpir error code; nothing
+ *    aborts the process. gpir_strerror() names the code.
+ *
+ * Array layouts (row-major, last index fastest; the paper's p-major layout of
+ * Sec. 2.3 / Sec. 5.1.2, every polynomial's N points contiguous):
+ *    db  [D0][D1][L][N]          DB[i][j], NTT form           (Sec. 2.2)
+ *    ct  [B][D0][2][L][N]        client c, selection ct i, polynomial r
+ *    out [B][D1][2][L][N]        client c, output ct j, polynomial r
+ */
+#ifndef GPIR_H
+#define GPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define GPIR_OK          0
+#define GPIR_EINVAL     -1  /* bad argument: shape, pointer, params, path   */
+#define GPIR_ERANGE     -2  /* a database residue >= its limb's prime       */
+#define GPIR_ENOMEM     -3  /* device or host allocation failed             */
+#define GPIR_ECUDA      -4  /* a CUDA runtime call failed                   */
+#define GPIR_ETIMEOUT   -5  /* a bounded wait (host or device) expired      */
+#define GPIR_ENOTSUP    -6  /* path not prepared for this database / device */
+
+/* ---- compute paths (also usable as a bit mask at upload) ---------------- */
+#define GPIR_PATH_AUTO      0  /* fastest prepared path for the shape        */
+#define GPIR_PATH_CUDACORE  1  /* 32x32->64-bit IMAD products, CUDA cores     */
+#define GPIR_PATH_IMMA      2  /* INT8 tensor cores (mma.sync u8), byte limbs */
+#define GPIR_PATH_TC        4  /* tcgen05 bf16 tensor cores, signed 8-bit
+                                  digits, exact fp32 partial sums            */
+#define GPIR_PATH_ALL       7
+
+/* Limits enforced by gpir_params_create. */
+#define GPIR_MAX_LIMBS      8
+#define GPIR_MIN_N          4
+#define GPIR_MAX_N      65536
+#define GPIR_MAX_PRIME_BITS 28   /* q < 2^28: every accumulator bound below
+                                    is proven for this width               */
+
+typedef struct gpir_params gpir_params_t;
+typedef struct gpir_db gpir_db_t;
+
+/* One RowSel problem of a multi-job launch: `batch` clients against `db`. */
+typedef struct gpir_job {
+  const gpir_db_t *db;
+  uint32_t batch;          /* B >= 1                                         */
+  uint32_t reserved;
+  const uint32_t *ct;      /* device, [B][D0][2][L][N]                       */
+  uint32_t *out;           /* device, [B][D1][2][L][N]                       */
+} gpir_job_t;
+
+/* Ring and RNS parameters (Sec. 2.4.1): ring degree n (power of two in
+ * [GPIR_MIN_N, GPIR_MAX_N]) and num_limbs primes, each prime, below
+ * 2^GPIR_MAX_PRIME_BITS and equal to 1 mod 2n (NTT-friendly). The primes are
+ * copied. Returns GPIR_EINVAL if any check fails. Host-only, synchronous. */
+int gpir_params_create(uint32_t n, uint32_t num_limbs, const uint32_t *primes,
+                       gpir_params_t **out);
+int gpir_params_destroy(gpir_params_t *params);
+
+/* Make an NTT-form database resident on the current device (Sec. 2.2: DB is
+ * D0 x D1 plaintext polynomials, stored after the NTT). `db_ntt` is
+ * [D0][D1][L][N] uint32, on the device if db_on_device != 0, else on the
+ * host. `path_mask` (GPIR_PATH_* bits, 0 = all) selects which packed layouts
+ * are built; each path reads only its own layout. Every residue is checked
+ * against its limb's prime: GPIR_ERANGE if any is >= q_l. The database is
+ * prepared once, before queries (the paper transposes its DB offline, Sec.
+ * 5.2.1), so this call synchronizes `stream`. The caller keeps ownership of
+ * `db_ntt`; the handle owns the device copies until gpir_db_free. */
+int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1,
+                   const uint32_t *db_ntt, int db_on_device, uint32_t path_mask,
+                   void *stream, gpir_db_t **out);
+int gpir_db_free(gpir_db_t *db);
+
+/* Device bytes held by the database handle (all packed layouts). */
+size_t gpir_db_device_bytes(const gpir_db_t *db);
+
+/* Batched RowSel (Sec. 2.2 and Sec. 5.1.1) on `stream`:
+ *   out[c][j][r][l][t] = sum_{i<D0} ct[c][i][r][l][t] * db[i][j][l][t] mod q_l
+ * for every client c < batch, output ct j < D1, polynomial r < 2, limb l and
+ * slot t. `ct_dev` and `out_dev` are device buffers in the layouts above and
+ * must not overlap. Inputs must be canonical residues (< q_l): this is a
+ * precondition, not checked, because a check would add a pass over the
+ * ciphertext stream. Results are canonical and identical for every path.
+ * GPIR_ENOTSUP if `path` was not prepared at upload. Asynchronous. */
+int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
+                      uint32_t *out_dev, int path, void *stream);
+
+/* Same computation with HOST buffers: copies ct host->device, runs RowSel and
+ * copies out device->host, all on `stream`, through a device workspace the
+ * handle owns (grown on demand; GPIR_ENOMEM if that fails). Returns after
+ * enqueueing; the host output is valid after gpir_sync(stream). Not safe to
+ * call concurrently on the same handle from several streams. */
+int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_host,
+                           uint32_t *out_host, int path, void *stream);
+
+/* Several RowSel problems (possibly different databases, uneven D0 / D1 and
+ * batch sizes) in ONE persistent launch: work tiles of all jobs are numbered
+ * into one global index space and claimed by resident CTAs from a device
+ * counter. All jobs must share the same params (N, L, primes). Asynchronous.
+ * The launch is capturable in a CUDA graph. */
+int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream);
+
+/* Wait for `stream` for at most timeout_ms milliseconds (0 = no limit).
+ * GPIR_ETIMEOUT if the stream is still busy, or if a kernel of this library
+ * reported that one of its bounded device-side waits expired; GPIR_ECUDA if
+ * the stream reported an error. */
+int gpir_sync(void *stream, uint32_t timeout_ms);
+
+/* Autotuner: time every compiled tile variant of `path` (three runs each,
+ * after a warm-up) for `batch` clients against this database, using the
+ * caller's device buffers ct_dev / out_dev (layouts as in gpir_rowsel_batch;
+ * out_dev is overwritten), and remember the fastest for (path, batch); later
+ * calls with that batch use it. Synchronizes `stream`. `*variant_out` (may be
+ * NULL) receives the chosen variant id. */
+int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
+                  uint32_t *out_dev, int path, void *stream, int *variant_out);
+
+/* Number of kernel variants compiled for `path` and the id in use for a
+ * shape (-1 if none chosen yet). Host-only. */
+int gpir_num_variants(int path);
+int gpir_selected_variant(const gpir_db_t *db, uint32_t batch, int path);
+/* Force a variant for (path, batch, D0, D1) of this database (testing). */
+int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant);
+
+/* Fill `count` uint32 residues on the device: element f gets
+ * SplitMix64-stream value (f + start) of (seed, tag) mod q_l, with
+ * l = ((f + start) / inner) % num_limbs -- the synthetic-input generator,
+ * identical to the host one. Asynchronous. */
+int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_t seed,
+                      uint64_t tag, const gpir_params_t *params, uint64_t inner,
+                      void *stream);
+
+const char *gpir_strerror(int code);
+/* Text of the last CUDA runtime error that made a call of this thread return
+ * GPIR_ECUDA or GPIR_ENOMEM ("no error" if none). */
+const char *gpir_last_cuda_error(void);
+/* Library version: major*10000 + minor*100 + patch. */
+int gpir_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPIR_H */

@@ -1,0 +1,482 @@
+// C ABI of libgpir.so: parameter checks, database residency, dispatch to the
+// RowSel kernels, host-buffer entry point, bounded synchronization.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gpir {
+
+static __device__ unsigned int g_device_error = 0;
+
+static thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+
+int set_cuda_error(cudaError_t e) {
+  t_last_cuda_error = e;
+  if (e == cudaErrorMemoryAllocation) return GPIR_ENOMEM;
+  return GPIR_ECUDA;
+}
+
+unsigned int *device_error_word() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::mutex mu;
+  static std::map<int, unsigned int *> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+  cache[dev] = (unsigned int *)p;
+  return (unsigned int *)p;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+int encode_tiled(CUtensorMap *map, CUtensorMapDataType dt, const void *base, int rank, const uint64_t *dims,
+                 const uint64_t *strides_bytes, const uint32_t *box, CUtensorMapSwizzle swz) {
+  auto fn = get_encode();
+  if (!fn) return GPIR_ECUDA;
+  if (((uintptr_t)base & 15u) != 0) return GPIR_EINVAL;
+  for (int i = 0; i < rank - 1; ++i)
+    if (strides_bytes[i] % 16 != 0) return GPIR_EINVAL;
+  cuuint64_t gd[5];
+  cuuint64_t gs[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+    es[i] = 1;
+  }
+  for (int i = 0; i < rank - 1; ++i) gs[i] = strides_bytes[i];
+  CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void *>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? GPIR_OK : GPIR_EINVAL;
+}
+
+int encode_tiled_u32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                     const uint64_t *strides_bytes, const uint32_t *box) {
+  return encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, base, rank, dims, strides_bytes, box,
+                      CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+// ---- device helpers for upload / synthetic fill ---------------------------
+
+__global__ void range_check_kernel(const uint32_t *__restrict__ v, uint64_t count, uint32_t N, uint32_t L,
+                                   LimbTable limbs, unsigned int *bad) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned int local = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    uint32_t l = (uint32_t)((i / N) % L);
+    local |= (v[i] >= limbs.m[l].q) ? 1u : 0u;
+  }
+  if (local) atomicOr(bad, 1u);
+}
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void fill_uniform_kernel(uint32_t *__restrict__ dst, uint64_t count, uint64_t start, uint64_t key,
+                                    uint64_t inner, uint32_t L, LimbTable limbs) {
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    uint64_t f = start + i;
+    uint64_t v = splitmix_mix(key + (f + 1) * 0x9E3779B97F4A7C15ull);
+    uint32_t l = (uint32_t)((f / inner) % L);
+    dst[i] = reduce64(v, limbs.m[l].q, limbs.m[l].mu);
+  }
+}
+
+static uint64_t host_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static bool is_prime_u32(uint32_t n) {
+  if (n < 2) return false;
+  if (n % 2 == 0) return n == 2;
+  for (uint32_t d = 3; (uint64_t)d * d <= n; d += 2)
+    if (n % d == 0) return false;
+  return true;
+}
+
+static int pick_variant(const gpir_db *db, uint32_t batch, int path) {
+  {
+    std::lock_guard<std::mutex> lk(*db->mu);
+    auto it = db->variants->find({path, batch});
+    if (it != db->variants->end()) return it->second;
+  }
+  switch (path) {
+    case GPIR_PATH_CUDACORE: return rowsel_cc_default_variant(batch, db->d0, db->d1);
+    case GPIR_PATH_IMMA: return rowsel_imma_default_variant(batch, db->d0, db->d1);
+    case GPIR_PATH_TC: return rowsel_tc_default_variant(batch, db->d0, db->d1);
+  }
+  return -1;
+}
+
+static int resolve_path(const gpir_db *db, int path) {
+  if (path == GPIR_PATH_AUTO) {
+    if (db->path_mask & GPIR_PATH_TC) return GPIR_PATH_TC;
+    if (db->path_mask & GPIR_PATH_CUDACORE) return GPIR_PATH_CUDACORE;
+    if (db->path_mask & GPIR_PATH_IMMA) return GPIR_PATH_IMMA;
+    return -1;
+  }
+  if (path != GPIR_PATH_CUDACORE && path != GPIR_PATH_IMMA && path != GPIR_PATH_TC) return -1;
+  if (!(db->path_mask & path)) return -2;
+  return path;
+}
+
+int dispatch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int path, int variant,
+             cudaStream_t s) {
+  switch (path) {
+    case GPIR_PATH_CUDACORE: return rowsel_cc_launch(db, batch, ct, out, variant, s);
+    case GPIR_PATH_IMMA: return rowsel_imma_launch(db, batch, ct, out, variant, s);
+    case GPIR_PATH_TC: return rowsel_tc_launch(db, batch, ct, out, variant, s);
+  }
+  return GPIR_EINVAL;
+}
+
+static int num_variants(int path) {
+  switch (path) {
+    case GPIR_PATH_CUDACORE: return rowsel_cc_num_variants();
+    case GPIR_PATH_IMMA: return rowsel_imma_num_variants();
+    case GPIR_PATH_TC: return rowsel_tc_num_variants();
+  }
+  return 0;
+}
+
+}  // namespace gpir
+
+using namespace gpir;
+
+extern "C" {
+
+int gpir_version(void) { return 100; }
+
+const char *gpir_last_cuda_error(void) { return cudaGetErrorString(t_last_cuda_error); }
+
+const char *gpir_strerror(int code) {
+  switch (code) {
+    case GPIR_OK: return "ok";
+    case GPIR_EINVAL: return "invalid argument";
+    case GPIR_ERANGE: return "database residue not below its prime";
+    case GPIR_ENOMEM: return "out of memory";
+    case GPIR_ECUDA: return "CUDA runtime error";
+    case GPIR_ETIMEOUT: return "bounded wait expired";
+    case GPIR_ENOTSUP: return "path not prepared or not supported";
+  }
+  return "unknown gpir error";
+}
+
+int gpir_params_create(uint32_t n, uint32_t num_limbs, const uint32_t *primes, gpir_params_t **out) {
+  if (!out || !primes) return GPIR_EINVAL;
+  *out = nullptr;
+  if (n < GPIR_MIN_N || n > GPIR_MAX_N || (n & (n - 1)) != 0) return GPIR_EINVAL;
+  if (num_limbs < 1 || num_limbs > GPIR_MAX_LIMBS) return GPIR_EINVAL;
+  for (uint32_t l = 0; l < num_limbs; ++l) {
+    uint32_t q = primes[l];
+    if (q < 3 || q >= (1u << GPIR_MAX_PRIME_BITS)) return GPIR_EINVAL;
+    if ((q - 1) % (2 * n) != 0) return GPIR_EINVAL;
+    if (!is_prime_u32(q)) return GPIR_EINVAL;
+  }
+  gpir_params *p = new (std::nothrow) gpir_params;
+  if (!p) return GPIR_ENOMEM;
+  memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->num_limbs = num_limbs;
+  for (uint32_t l = 0; l < num_limbs; ++l) {
+    p->primes[l] = primes[l];
+    p->limbs.m[l].q = primes[l];
+    p->limbs.m[l].mu = ~0ull / primes[l];  // floor((2^64 - 1) / q) = floor(2^64 / q) for q not a power of 2
+  }
+  *out = p;
+  return GPIR_OK;
+}
+
+int gpir_params_destroy(gpir_params_t *params) {
+  delete params;
+  return GPIR_OK;
+}
+
+int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1, const uint32_t *db_ntt, int db_on_device,
+                   uint32_t path_mask, void *stream, gpir_db_t **out) {
+  if (!params || !db_ntt || !out || d0 == 0 || d1 == 0) return GPIR_EINVAL;
+  *out = nullptr;
+  if (path_mask == 0) path_mask = GPIR_PATH_ALL;
+  if (path_mask & ~(uint32_t)GPIR_PATH_ALL) return GPIR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t count = (uint64_t)d0 * d1 * params->num_limbs * params->n;
+  const size_t bytes = count * 4;
+  gpir_db *db = new (std::nothrow) gpir_db;
+  if (!db) return GPIR_ENOMEM;
+  memset((void *)db, 0, sizeof(*db));
+  db->params = *params;
+  db->d0 = d0;
+  db->d1 = d1;
+  db->path_mask = path_mask;
+  cudaGetDevice(&db->device);
+  db->variants = new std::map<std::pair<int, uint32_t>, int>();
+  db->mu = new std::mutex();
+  int rc = GPIR_OK;
+  unsigned int *bad = nullptr;
+  cudaError_t e = cudaMalloc(&db->db_pmajor, bytes);
+  if (e != cudaSuccess) {
+    rc = set_cuda_error(e);
+    goto fail;
+  }
+  e = cudaMemcpyAsync(db->db_pmajor, db_ntt, bytes, db_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      s);
+  if (e != cudaSuccess) {
+    rc = set_cuda_error(e);
+    goto fail;
+  }
+  e = cudaMallocAsync(&bad, sizeof(unsigned int), s);
+  if (e != cudaSuccess) {
+    rc = set_cuda_error(e);
+    goto fail;
+  }
+  cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+  range_check_kernel<<<sm_count() * 4, 256, 0, s>>>(db->db_pmajor, count, params->n, params->num_limbs,
+                                                     params->limbs, bad);
+  {
+    unsigned int hbad = 0;
+    e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(bad, s);
+    bad = nullptr;
+    if (e != cudaSuccess) {
+      rc = set_cuda_error(e);
+      goto fail;
+    }
+    if (hbad) {
+      rc = GPIR_ERANGE;
+      goto fail;
+    }
+  }
+  if (path_mask & GPIR_PATH_TC) {
+    rc = rowsel_tc_prepare(db, s);
+    if (rc != GPIR_OK) goto fail;
+  }
+  *out = db;
+  return GPIR_OK;
+fail:
+  gpir_db_free(db);
+  return rc;
+}
+
+int gpir_db_free(gpir_db_t *db) {
+  if (!db) return GPIR_OK;
+  if (db->db_pmajor) cudaFree(db->db_pmajor);
+  if (db->db_digits) cudaFree(db->db_digits);
+  if (db->ws_ct) cudaFree(db->ws_ct);
+  if (db->ws_out) cudaFree(db->ws_out);
+  delete db->variants;
+  delete db->mu;
+  delete db;
+  return GPIR_OK;
+}
+
+size_t gpir_db_device_bytes(const gpir_db_t *db) {
+  if (!db) return 0;
+  size_t b = (size_t)db->d0 * db->d1 * db->params.num_limbs * db->params.n * 4;
+  return b + db->db_digits_bytes;
+}
+
+int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
+                      void *stream) {
+  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  int p = resolve_path(db, path);
+  if (p == -1) return GPIR_EINVAL;
+  if (p == -2) return GPIR_ENOTSUP;
+  const size_t ct_bytes = (size_t)batch * db->d0 * 2 * db->params.num_limbs * db->params.n * 4;
+  const size_t out_bytes = (size_t)batch * db->d1 * 2 * db->params.num_limbs * db->params.n * 4;
+  const uintptr_t a0 = (uintptr_t)ct_dev, a1 = a0 + ct_bytes, b0 = (uintptr_t)out_dev, b1 = b0 + out_bytes;
+  if (a0 < b1 && b0 < a1) return GPIR_EINVAL;  // overlapping input / output
+  if ((a0 & 15u) || (b0 & 15u)) return GPIR_EINVAL;
+  return dispatch(db, batch, ct_dev, out_dev, p, pick_variant(db, batch, p), (cudaStream_t)stream);
+}
+
+int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t *ct_host, uint32_t *out_host,
+                           int path, void *stream) {
+  if (!db_c || !ct_host || !out_host || batch == 0) return GPIR_EINVAL;
+  gpir_db *db = const_cast<gpir_db *>(db_c);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ct_bytes = (size_t)batch * db->d0 * 2 * db->params.num_limbs * db->params.n * 4;
+  const size_t out_bytes = (size_t)batch * db->d1 * 2 * db->params.num_limbs * db->params.n * 4;
+  cudaError_t e;
+  if (db->ws_ct_bytes < ct_bytes) {
+    if (db->ws_ct) {
+      cudaStreamSynchronize(s);
+      cudaFree(db->ws_ct);
+    }
+    db->ws_ct = nullptr;
+    db->ws_ct_bytes = 0;
+    e = cudaMalloc(&db->ws_ct, ct_bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    db->ws_ct_bytes = ct_bytes;
+  }
+  if (db->ws_out_bytes < out_bytes) {
+    if (db->ws_out) {
+      cudaStreamSynchronize(s);
+      cudaFree(db->ws_out);
+    }
+    db->ws_out = nullptr;
+    db->ws_out_bytes = 0;
+    e = cudaMalloc(&db->ws_out, out_bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    db->ws_out_bytes = out_bytes;
+  }
+  e = cudaMemcpyAsync(db->ws_ct, ct_host, ct_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  int rc = gpir_rowsel_batch(db, batch, db->ws_ct, db->ws_out, path, stream);
+  if (rc != GPIR_OK) return rc;
+  e = cudaMemcpyAsync(out_host, db->ws_out, out_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  return GPIR_OK;
+}
+
+int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream) {
+  if (!jobs || njobs == 0) return GPIR_EINVAL;
+  for (uint32_t k = 0; k < njobs; ++k) {
+    if (!jobs[k].db || !jobs[k].ct || !jobs[k].out || jobs[k].batch == 0) return GPIR_EINVAL;
+    const gpir_params &a = jobs[0].db->params, &b = jobs[k].db->params;
+    if (a.n != b.n || a.num_limbs != b.num_limbs || memcmp(a.primes, b.primes, sizeof(a.primes)) != 0)
+      return GPIR_EINVAL;
+  }
+  return rowsel_multi_launch(jobs, njobs, path, (cudaStream_t)stream);
+}
+
+int gpir_sync(void *stream, uint32_t timeout_ms) {
+  cudaStream_t s = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return set_cuda_error(e);
+    if (timeout_ms && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return GPIR_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  unsigned int *w = device_error_word();
+  if (!w) return GPIR_ECUDA;
+  unsigned int h = 0;
+  cudaError_t e = cudaMemcpy(&h, w, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (h != 0) {
+    unsigned int zero = 0;
+    cudaMemcpy(w, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    return GPIR_ETIMEOUT;
+  }
+  return GPIR_OK;
+}
+
+int gpir_num_variants(int path) { return num_variants(path); }
+
+int gpir_selected_variant(const gpir_db_t *db, uint32_t batch, int path) {
+  if (!db) return -1;
+  std::lock_guard<std::mutex> lk(*db->mu);
+  auto it = db->variants->find({path, batch});
+  return it == db->variants->end() ? -1 : it->second;
+}
+
+int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant) {
+  if (!db || variant < 0 || variant >= num_variants(path)) return GPIR_EINVAL;
+  std::lock_guard<std::mutex> lk(*db->mu);
+  (*db->variants)[{path, batch}] = variant;
+  return GPIR_OK;
+}
+
+int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
+                  void *stream, int *variant_out) {
+  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  int p = resolve_path(db, path);
+  if (p == -1) return GPIR_EINVAL;
+  if (p == -2) return GPIR_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return GPIR_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return GPIR_ECUDA;
+  }
+  int best = -1;
+  float best_ms = 1e30f;
+  const int nv = num_variants(p);
+  for (int v = 0; v < nv; ++v) {
+    int rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);  // warm-up (and support check)
+    if (rc != GPIR_OK) continue;
+    float tot = 0.f;
+    bool okv = true;
+    for (int rep = 0; rep < 3 && okv; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);
+      cudaEventRecord(e1, s);
+      if (rc != GPIR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        okv = false;
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (okv && tot < best_ms) {
+      best_ms = tot;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return GPIR_ENOTSUP;
+  {
+    std::lock_guard<std::mutex> lk(*db->mu);
+    (*db->variants)[{p, batch}] = best;
+  }
+  if (variant_out) *variant_out = best;
+  return GPIR_OK;
+}
+
+int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_t seed, uint64_t tag,
+                      const gpir_params_t *params, uint64_t inner, void *stream) {
+  if (!dst_dev || !params || inner == 0) return GPIR_EINVAL;
+  if (count == 0) return GPIR_OK;
+  const uint64_t key = host_mix((seed * 0x9E3779B97F4A7C15ull) ^ ((tag + 1) * 0xD1B54A32D192ED03ull));
+  fill_uniform_kernel<<<sm_count() * 8, 256, 0, (cudaStream_t)stream>>>(dst_dev, count, start, key, inner,
+                                                                         params->num_limbs, params->limbs);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+}  // extern "C"

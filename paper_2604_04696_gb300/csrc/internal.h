@@ -1,0 +1,96 @@
+// Internal declarations shared by the translation units of libgpir.so.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/gpir.h"
+
+namespace gpir {
+
+// Per-limb modulus data passed by value to kernels.
+struct Modulus {
+  uint32_t q;
+  uint32_t pad;
+  uint64_t mu;   // floor(2^64 / q): Barrett constant for 64-bit reduction
+};
+
+struct LimbTable {
+  Modulus m[GPIR_MAX_LIMBS];
+};
+
+// Shape of one RowSel problem (Sec. 2.3 extents): M = 2 * batch rows,
+// K = D0 reduction, Nc = D1 columns, per (limb, slot) point.
+struct Shape {
+  uint32_t batch, d0, d1, L, N;
+};
+
+}  // namespace gpir
+
+struct gpir_params {
+  uint32_t n;
+  uint32_t num_limbs;
+  uint32_t primes[GPIR_MAX_LIMBS];
+  gpir::LimbTable limbs;
+};
+
+struct gpir_db {
+  gpir_params params;
+  uint32_t d0, d1;
+  uint32_t path_mask;
+  int device;
+  // CUDA-core and IMMA paths read the p-major database as uploaded.
+  uint32_t *db_pmajor;          // [D0][D1][L][N]
+  // tcgen05 path: signed 8-bit digits as bf16, slot-major (see rowsel_tc.cu).
+  uint16_t *db_digits;
+  size_t db_digits_bytes;
+  CUtensorMap db_map_cc;        // TMA descriptor over db_pmajor (CUDA-core path)
+  // Host-buffer entry point workspace.
+  uint32_t *ws_ct, *ws_out;
+  size_t ws_ct_bytes, ws_out_bytes;
+  // Autotune cache: (path, batch) -> variant
+  std::map<std::pair<int, uint32_t>, int> *variants;
+  std::mutex *mu;
+};
+
+namespace gpir {
+
+// Error helpers
+int set_cuda_error(cudaError_t e);
+
+// TMA descriptor encoding (driver entry point resolved at first use).
+int encode_tiled_u32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                     const uint64_t *strides_bytes /* rank-1 entries */, const uint32_t *box);
+int encode_tiled(CUtensorMap *map, CUtensorMapDataType dt, const void *base, int rank,
+                 const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box,
+                 CUtensorMapSwizzle swz);
+
+// Device error word written by bounded waits in kernels (0 = ok).
+unsigned int *device_error_word();
+int sm_count();
+
+// Path entry points (one per translation unit).
+int rowsel_cc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out,
+                     int variant, cudaStream_t stream);
+int rowsel_cc_num_variants();
+int rowsel_cc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
+
+int rowsel_imma_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out,
+                       int variant, cudaStream_t stream);
+int rowsel_imma_num_variants();
+int rowsel_imma_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
+
+int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream);
+int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out,
+                     int variant, cudaStream_t stream);
+int rowsel_tc_num_variants();
+int rowsel_tc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
+
+int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaStream_t stream);
+
+}  // namespace gpir

@@ -1,0 +1,200 @@
+"""Thin ctypes binding of libgpir.so: the C ABI of include/gpir.h, same names.
+
+Argument marshalling only: every step of RowSel runs in the library's CUDA
+kernels. Device buffers may be passed as integers (device addresses) or as
+objects with a ``data_ptr()`` method (torch tensors); streams as integers
+(cudaStream_t) or objects with a ``cuda_stream`` attribute. There is no CPU
+fallback: if the library cannot be loaded, importing this module raises.
+"""
+
+import ctypes
+import os
+
+from . import _build
+
+GPIR_OK = 0
+GPIR_EINVAL = -1
+GPIR_ERANGE = -2
+GPIR_ENOMEM = -3
+GPIR_ECUDA = -4
+GPIR_ETIMEOUT = -5
+GPIR_ENOTSUP = -6
+
+GPIR_PATH_AUTO = 0
+GPIR_PATH_CUDACORE = 1
+GPIR_PATH_IMMA = 2
+GPIR_PATH_TC = 4
+GPIR_PATH_ALL = 7
+
+GPIR_MAX_LIMBS = 8
+GPIR_MIN_N = 4
+GPIR_MAX_N = 65536
+GPIR_MAX_PRIME_BITS = 28
+
+
+class GpirError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)%s" % (what, _strerror(code), code, _cuda_detail(code)))
+
+
+class gpir_job_t(ctypes.Structure):
+    _fields_ = [("db", ctypes.c_void_p), ("batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("ct", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libgpir.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, U32, U64, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "gpir_params_create": (I, [U32, U32, ctypes.POINTER(U32), ctypes.POINTER(P)]),
+        "gpir_params_destroy": (I, [P]),
+        "gpir_db_upload": (I, [P, U32, U32, P, I, U32, P, ctypes.POINTER(P)]),
+        "gpir_db_free": (I, [P]),
+        "gpir_db_device_bytes": (ctypes.c_size_t, [P]),
+        "gpir_rowsel_batch": (I, [P, U32, P, P, I, P]),
+        "gpir_rowsel_batch_host": (I, [P, U32, P, P, I, P]),
+        "gpir_rowsel_multi": (I, [ctypes.POINTER(gpir_job_t), U32, I, P]),
+        "gpir_sync": (I, [P, U32]),
+        "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
+        "gpir_num_variants": (I, [I]),
+        "gpir_selected_variant": (I, [P, U32, I]),
+        "gpir_set_variant": (I, [P, U32, I, I]),
+        "gpir_fill_uniform": (I, [P, U64, U64, U64, U64, P, U64, P]),
+        "gpir_strerror": (ctypes.c_char_p, [I]),
+        "gpir_last_cuda_error": (ctypes.c_char_p, []),
+        "gpir_version": (I, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _strerror(code):
+    return lib.gpir_strerror(code).decode()
+
+
+def _cuda_detail(code):
+    if code in (GPIR_ECUDA, GPIR_ENOMEM):
+        return ": " + lib.gpir_last_cuda_error().decode()
+    return ""
+
+
+def _check(rc, what):
+    if rc != GPIR_OK:
+        raise GpirError(rc, what)
+    return rc
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):          # numpy array (host)
+        return x.ctypes.data
+    return int(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def gpir_params_create(n, primes):
+    arr = (ctypes.c_uint32 * len(primes))(*[int(q) for q in primes])
+    h = ctypes.c_void_p()
+    _check(lib.gpir_params_create(int(n), len(primes), arr, ctypes.byref(h)), "gpir_params_create")
+    return h
+
+
+def gpir_params_destroy(params):
+    return lib.gpir_params_destroy(params)
+
+
+def gpir_db_upload(params, d0, d1, db_ntt, on_device, path_mask=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib.gpir_db_upload(params, int(d0), int(d1), _ptr(db_ntt), 1 if on_device else 0, int(path_mask),
+                              _stream(stream), ctypes.byref(h)), "gpir_db_upload")
+    return h
+
+
+def gpir_db_free(db):
+    return lib.gpir_db_free(db)
+
+
+def gpir_db_device_bytes(db):
+    return lib.gpir_db_device_bytes(db)
+
+
+def gpir_rowsel_batch(db, batch, ct_dev, out_dev, path=GPIR_PATH_AUTO, stream=None):
+    return _check(lib.gpir_rowsel_batch(db, int(batch), _ptr(ct_dev), _ptr(out_dev), int(path), _stream(stream)),
+                  "gpir_rowsel_batch")
+
+
+def gpir_rowsel_batch_host(db, batch, ct_host, out_host, path=GPIR_PATH_AUTO, stream=None):
+    return _check(lib.gpir_rowsel_batch_host(db, int(batch), _ptr(ct_host), _ptr(out_host), int(path),
+                                             _stream(stream)), "gpir_rowsel_batch_host")
+
+
+def gpir_rowsel_multi(jobs, path=GPIR_PATH_AUTO, stream=None):
+    """jobs: sequence of (db_handle, batch, ct_dev, out_dev)."""
+    arr = (gpir_job_t * len(jobs))()
+    for k, (db, batch, ct, out) in enumerate(jobs):
+        arr[k].db = db.value if isinstance(db, ctypes.c_void_p) else db
+        arr[k].batch = int(batch)
+        arr[k].ct = _ptr(ct)
+        arr[k].out = _ptr(out)
+    return _check(lib.gpir_rowsel_multi(arr, len(jobs), int(path), _stream(stream)), "gpir_rowsel_multi")
+
+
+def gpir_sync(stream=None, timeout_ms=0):
+    return _check(lib.gpir_sync(_stream(stream), int(timeout_ms)), "gpir_sync")
+
+
+def gpir_sync_rc(stream=None, timeout_ms=0):
+    """gpir_sync returning the raw code instead of raising."""
+    return lib.gpir_sync(_stream(stream), int(timeout_ms))
+
+
+def gpir_autotune(db, batch, ct_dev, out_dev, path, stream=None):
+    v = ctypes.c_int(-1)
+    _check(lib.gpir_autotune(db, int(batch), _ptr(ct_dev), _ptr(out_dev), int(path), _stream(stream),
+                             ctypes.byref(v)), "gpir_autotune")
+    return v.value
+
+
+def gpir_num_variants(path):
+    return lib.gpir_num_variants(int(path))
+
+
+def gpir_selected_variant(db, batch, path):
+    return lib.gpir_selected_variant(db, int(batch), int(path))
+
+
+def gpir_set_variant(db, batch, path, variant):
+    return _check(lib.gpir_set_variant(db, int(batch), int(path), int(variant)), "gpir_set_variant")
+
+
+def gpir_fill_uniform(dst_dev, count, start, seed, tag, params, inner, stream=None):
+    return _check(lib.gpir_fill_uniform(_ptr(dst_dev), int(count), int(start), int(seed), int(tag), params,
+                                        int(inner), _stream(stream)), "gpir_fill_uniform")
+
+
+def gpir_strerror(code):
+    return _strerror(code)
+
+
+def gpir_version():
+    return lib.gpir_version()

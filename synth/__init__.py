@@ -13,10 +13,12 @@ published odd multipliers) and GAMMA = 0x9E3779B97F4A7C15.
 A residue mod q is value(i) mod q (bias below 2^-36 for q < 2^28).
 """
 
-from .gen import (GAMMA, mix64, stream_key, uniform_u64, uniform_residues,
+from .gen import (GAMMA, mix64, stream_key, uniform_u64, uniform_residues, residues_at,
+                  uniform_u64_at, ct_slots, db_slots,
                   ct_tensor, db_tensor, TAG_DB, TAG_CT, TAG_SECRET, TAG_MASK,
                   toy_rlwe_selection, config_shapes, CONFIGS, PRIMES_28)
 
-__all__ = ["GAMMA", "mix64", "stream_key", "uniform_u64", "uniform_residues",
+__all__ = ["GAMMA", "mix64", "stream_key", "uniform_u64", "uniform_residues", "residues_at",
+           "uniform_u64_at", "ct_slots", "db_slots",
            "ct_tensor", "db_tensor", "TAG_DB", "TAG_CT", "TAG_SECRET", "TAG_MASK",
            "toy_rlwe_selection", "config_shapes", "CONFIGS", "PRIMES_28"]

@@ -108,3 +108,40 @@ def config_shapes(name: str):
     c = dict(CONFIGS[name])
     c["primes"] = PRIMES_28[:c["L"]]
     return c
+
+
+def residues_at(seed: int, tag: int, flat_idx, limb, primes) -> np.ndarray:
+    """value(f) mod q_limb for arbitrary flat indices f (random access into a
+    tensor generated by uniform_residues with the same seed and tag)."""
+    f = np.asarray(flat_idx, dtype=np.uint64)
+    v = uniform_u64_at(seed, tag, f)
+    qs = np.asarray(primes, dtype=np.uint64)[np.asarray(limb, dtype=np.int64)]
+    return (v % qs).astype(np.uint32)
+
+
+def uniform_u64_at(seed: int, tag: int, flat_idx) -> np.ndarray:
+    key = np.uint64(stream_key(seed, tag))
+    f = np.asarray(flat_idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix64_np(key + (f + np.uint64(1)) * np.uint64(GAMMA))
+
+
+def ct_slots(seed: int, B: int, D0: int, L: int, N: int, primes, slots) -> np.ndarray:
+    """ct_tensor(...)[..., l, t] for the given (l, t) slot pairs: [B][D0][2][S]."""
+    c = np.arange(B)[:, None, None, None]
+    i = np.arange(D0)[None, :, None, None]
+    r = np.arange(2)[None, None, :, None]
+    ls = np.array([s[0] for s in slots])[None, None, None, :]
+    ts = np.array([s[1] for s in slots])[None, None, None, :]
+    f = (((c * D0 + i) * 2 + r) * L + ls) * N + ts
+    return residues_at(seed, TAG_CT, f, np.broadcast_to(ls, f.shape), primes)
+
+
+def db_slots(seed: int, D0: int, D1: int, L: int, N: int, primes, slots) -> np.ndarray:
+    """db_tensor(...)[..., l, t] for the given (l, t) slot pairs: [D0][D1][S]."""
+    i = np.arange(D0)[:, None, None]
+    j = np.arange(D1)[None, :, None]
+    ls = np.array([s[0] for s in slots])[None, None, :]
+    ts = np.array([s[1] for s in slots])[None, None, :]
+    f = ((i * D1 + j) * L + ls) * N + ts
+    return residues_at(seed, TAG_DB, f, np.broadcast_to(ls, f.shape), primes)

@@ -1,0 +1,151 @@
+"""Host-side logic without a GPU: sizes, the input generator, the C ABI's
+exported symbols and its argument checks."""
+
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2604_04696_gb300 import sizes
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+def test_sizes_match_paper():
+    g = _gold("paper_sizes.json")
+    assert sizes.poly_bytes(4096, 4) == g["a_poly_bytes"]["value"]
+    assert sizes.ct_bytes(4096, 4) == g["ct_bytes"]["value"]
+    assert sizes.db_bytes(1, 1, 4096, 4) == g["record_poly_bytes"]["value"]
+    assert sizes.raw_record_bytes(4096, 32) == g["record_raw_bytes"]["value"]
+    assert sizes.query_ct_bytes(32, 256, 4096, 4) == g["expanded_cts_batch32"]["value"]
+    assert sizes.naive_transpose_bytes(32, 256, 512, 4096, 4) == g["transpose_traffic_2gb_batch32"]["value"]
+    assert sizes.db_bytes(1, 1, 4096, 4) // sizes.raw_record_bytes(4096, 32) == g["storage_overhead"]["value"]
+    # 2 GB of raw records at 16 KB each with D0 = 256 gives D1 = 512
+    assert (2 << 30) // sizes.raw_record_bytes(4096, 32) // 256 == 512
+
+
+def test_workload_byte_counts():
+    # 4 GiB NTT-form DB at N=4096, 2 limbs, D0=1024, D1=128; 8 GiB of selection cts at B=128
+    assert sizes.db_bytes(1024, 128, 4096, 2) == 4 << 30
+    assert sizes.query_ct_bytes(128, 1024, 4096, 2) == 8 << 30
+    assert sizes.out_bytes(128, 128, 4096, 2) == 1 << 30
+    assert sizes.db_bytes(256, 64, 4096, 2) == 512 << 20
+    assert sizes.rowsel_modmacs(128, 1024, 128, 4096, 2) == 274877906944
+
+
+def test_splitmix64_published_vectors():
+    g = _gold("splitmix64_vectors.json")
+    for key, want in g.items():
+        if not key.startswith("seed_"):
+            continue
+        s = int(key[5:])
+        got = []
+        for _ in range(len(want)):
+            s = (s + synth.GAMMA) & ((1 << 64) - 1)
+            got.append(synth.mix64(s))
+        assert got == want
+
+
+def test_counter_stream_is_random_access():
+    a = synth.uniform_u64(5, 2, 0, 1000)
+    b = synth.uniform_u64(5, 2, 400, 100)
+    assert np.array_equal(a[400:500], b)
+    key = synth.stream_key(5, 2)
+    assert int(a[7]) == synth.mix64(key + 8 * synth.GAMMA)
+    assert not np.array_equal(synth.uniform_u64(5, 3, 0, 10), a[:10])
+
+
+def test_residues_in_range_and_limb_mapping():
+    primes = (17, 41)
+    x = synth.uniform_residues(3, 1, (3, 2, 8), primes, limb_axis=1)
+    assert x[:, 0].max() < 17 and x[:, 1].max() < 41
+    v = synth.uniform_u64(3, 1, 0, 48).reshape(3, 2, 8)
+    assert np.array_equal(x[:, 0], (v[:, 0] % 17).astype(np.uint32))
+    assert np.array_equal(x[:, 1], (v[:, 1] % 41).astype(np.uint32))
+
+
+def test_residues_roughly_uniform():
+    q = synth.PRIMES_28[0]
+    x = synth.uniform_residues(0, 2, (1, 200000), (q,), limb_axis=0).astype(np.float64).ravel()
+    assert abs(x.mean() / q - 0.5) < 0.005
+    hist = np.histogram(x, bins=16, range=(0, q))[0]
+    assert hist.min() > 0.9 * 200000 / 16
+
+
+# ---- C ABI (library loads on a CPU host; no call here touches CUDA) ---------
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2604_04696_gb300 import _build
+    _build.build()
+    from paper_2604_04696_gb300 import gpir
+    return gpir
+
+
+def test_every_header_symbol_is_exported(g):
+    with open(os.path.join(ROOT, "include", "gpir.h")) as fh:
+        hdr = fh.read()
+    declared = set(re.findall(r"\b(gpir_[a-z_0-9]+)\s*\(", hdr))
+    assert "gpir_rowsel_batch" in declared and len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(g.lib, name), name
+
+
+def test_params_checks(g):
+    q0, q1 = synth.PRIMES_28
+    p = g.gpir_params_create(4096, [q0, q1])
+    assert p.value
+    g.gpir_params_destroy(p)
+    bad = [
+        (4096, [q0 + 2]),                 # not prime
+        (4096, [268369921 + 8192 * 0 + 4096]),  # not 1 mod 2N
+        (3000, [q0]),                     # N not a power of two
+        (2, [17]),                        # N below the minimum
+        (131072, [q0]),                   # N above the maximum
+        (4096, [(1 << 28) + 8193]),       # prime too wide
+        (4096, []),                       # no limbs
+        (4096, [q0] * 9),                 # too many limbs
+    ]
+    for n, primes in bad:
+        with pytest.raises(g.GpirError) as ei:
+            g.gpir_params_create(n, primes)
+        assert ei.value.code == g.GPIR_EINVAL
+    assert g.gpir_params_create(4, [17, 41]).value
+    assert g.gpir_params_create(65536, [786433]).value   # 786433 = 12 * 2^16 + 1, prime
+
+
+def test_strerror_and_version(g):
+    assert g.gpir_version() == 100
+    for code in (g.GPIR_OK, g.GPIR_EINVAL, g.GPIR_ERANGE, g.GPIR_ENOMEM, g.GPIR_ECUDA, g.GPIR_ETIMEOUT,
+                 g.GPIR_ENOTSUP):
+        assert g.gpir_strerror(code) != "unknown gpir error"
+    assert g.gpir_strerror(-99) == "unknown gpir error"
+
+
+def test_null_arguments_rejected(g):
+    assert g.lib.gpir_rowsel_batch(None, 1, None, None, 0, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_rowsel_multi(None, 0, 0, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_db_upload(None, 1, 1, None, 0, 0, None, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_db_free(None) == g.GPIR_OK
+
+
+def test_slot_sampling_matches_full_tensors():
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 3, 5, 4, 2, 16
+    ct = synth.ct_tensor(7, B, D0, L, N, primes)
+    db = synth.db_tensor(7, D0, D1, L, N, primes)
+    slots = [(0, 3), (1, 15), (1, 0)]
+    cs = synth.ct_slots(7, B, D0, L, N, primes, slots)
+    ds = synth.db_slots(7, D0, D1, L, N, primes, slots)
+    for k, (l, t) in enumerate(slots):
+        assert np.array_equal(cs[..., k], ct[:, :, :, l, t])
+        assert np.array_equal(ds[..., k], db[:, :, l, t])

@@ -1,0 +1,234 @@
+"""GPU RowSel vs the CPU oracle, bit-exact (modular integer work: tolerance 0).
+
+All calls go through the C ABI (libgpir.so) via the ctypes binding."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+PATHS = {"cudacore": 1}
+
+
+@pytest.fixture(scope="module")
+def g():
+    from tests import gpu_util
+    return gpu_util.lib()
+
+
+def _avail_paths(g):
+    return [name for name, p in PATHS.items() if g.gpir_num_variants(p) > 0]
+
+
+def _check_full(g, B, D0, D1, L, N, primes, seed, path, variants=None):
+    from tests.gpu_util import DbHandle, to_dev, to_host, make_problem
+    ct, db = make_problem(seed, B, D0, D1, L, N, primes)
+    want = oracle.rowsel(ct, db, list(primes))
+    h = DbHandle(g, db, N, primes, path_mask=path)
+    try:
+        ct_d = to_dev(ct)
+        vs = variants if variants is not None else [None]
+        for v in vs:
+            if v is not None:
+                g.gpir_set_variant(h.h, B, path, v)
+            got = to_host(h.rowsel(ct_d, B, path))
+            assert np.array_equal(got, want), "mismatch path %d variant %s: %d of %d differ" % (
+                path, v, int((got != want).sum()), want.size)
+    finally:
+        h.close()
+
+
+SHAPES = [
+    # (B, D0, D1, L, N, primes)                      what it covers
+    (1, 16, 16, 1, 2048, synth.PRIMES_28[:1]),      # plain RowSel workload, seed 0
+    (3, 40, 24, 2, 64, synth.PRIMES_28),            # ragged rows / cols / clients
+    (9, 300, 70, 2, 128, synth.PRIMES_28),          # D0 crosses the 256-row reduction period
+    (2, 5, 3, 2, 8, (17, 97)),                      # ring smaller than a warp of slots
+    (1, 1, 1, 1, 4, (17,)),                         # degenerate 1 x 1
+    (5, 33, 65, 3, 32, (193, 257, 449)),            # three limbs
+    (17, 64, 17, 1, 96 * 0 + 64, (268369921,)),     # odd client count
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "B%d_D0%d_D1%d_L%d_N%d" % s[:5])
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_rowsel_vs_oracle(g, shape, path):
+    B, D0, D1, L, N, primes = shape
+    seed = 0 if (B, D0, D1, N) == (1, 16, 16, 2048) else 1000 + B + D0
+    if g.gpir_num_variants(PATHS[path]) == 0:
+        pytest.skip("path not built")
+    _check_full(g, B, D0, D1, L, N, primes, seed, PATHS[path])
+
+
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_every_variant(g, path):
+    p = PATHS[path]
+    nv = g.gpir_num_variants(p)
+    _check_full(g, 6, 70, 40, 2, 64, synth.PRIMES_28, 77, p, variants=list(range(nv)))
+
+
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_worst_case_accumulation(g, path):
+    """All residues q-1 with D0 = 2048: every product is maximal; result D0 mod q."""
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 2, 2048, 8, 2, 32
+    ct = np.empty((B, D0, 2, L, N), dtype=np.uint32)
+    db = np.empty((D0, D1, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        ct[:, :, :, l] = q - 1
+        db[:, :, l] = q - 1
+    h = DbHandle(g, db, N, primes, path_mask=PATHS[path])
+    try:
+        got = to_host(h.rowsel(to_dev(ct), B, PATHS[path]))
+    finally:
+        h.close()
+    for l, q in enumerate(primes):
+        assert np.all(got[:, :, :, l] == D0 % q)
+
+
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_one_hot_returns_row(g, path):
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 4, 50, 12, 2, 256
+    db = synth.db_tensor(5, D0, D1, L, N, primes)
+    istars = [0, 49, 17, 17]
+    ct = np.zeros((B, D0, 2, L, N), dtype=np.uint32)
+    for c, i in enumerate(istars):
+        ct[c, i] = 1
+    h = DbHandle(g, db, N, primes, path_mask=PATHS[path])
+    try:
+        got = to_host(h.rowsel(to_dev(ct), B, PATHS[path]))
+    finally:
+        h.close()
+    for c, i in enumerate(istars):
+        for r in range(2):
+            assert np.array_equal(got[c, :, r], db[i])
+
+
+def _sampled_full_size(g, name, path, n_slots=6):
+    """Full-size workload generated on the device; oracle on sampled slots."""
+    import torch
+    from tests.gpu_util import to_host
+    cfg = synth.config_shapes(name)
+    N, L, D0, D1, seed, primes = cfg["N"], cfg["L"], cfg["D0"], cfg["D1"], cfg["seed"], cfg["primes"]
+    B = cfg["B"] if isinstance(cfg["B"], int) else max(cfg["B"])
+    params = g.gpir_params_create(N, list(primes))
+    db_d = torch.empty(D0 * D1 * L * N, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(db_d, db_d.numel(), 0, seed, synth.TAG_DB, params, N)
+    ct_d = torch.empty(B * D0 * 2 * L * N, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(ct_d, ct_d.numel(), 0, seed, synth.TAG_CT, params, N)
+    h = g.gpir_db_upload(params, D0, D1, db_d, True, path)
+    del db_d
+    out = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
+    try:
+        g.gpir_rowsel_batch(h, B, ct_d, out, path)
+        torch.cuda.synchronize()
+        g.gpir_sync(None, 60000)
+        rng = np.random.default_rng(123)
+        slots = [(0, 0), (L - 1, N - 1)] + [(int(rng.integers(0, L)), int(rng.integers(0, N)))
+                                            for _ in range(n_slots - 2)]
+        ct_s = synth.ct_slots(seed, B, D0, L, N, primes, slots)        # [B][D0][2][S]
+        db_s = synth.db_slots(seed, D0, D1, L, N, primes, slots)       # [D0][D1][S]
+        got_all = out.view(B, D1, 2, L, N)
+        for k, (l, t) in enumerate(slots):
+            want = oracle.rowsel(ct_s[:, :, :, None, k:k + 1], db_s[:, :, None, k:k + 1], [primes[l]])
+            got = to_host(got_all[:, :, :, l, t].contiguous())
+            assert np.array_equal(got, want[:, :, :, 0, 0]), (l, t)
+    finally:
+        g.gpir_db_free(h)
+        g.gpir_params_destroy(params)
+
+
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_full_size_rowsel_32_clients_sampled(g, path):
+    _sampled_full_size(g, "c2_rowsel", PATHS[path])
+
+
+@pytest.mark.parametrize("path", ["cudacore"])
+def test_full_size_large_db_sampled(g, path):
+    _sampled_full_size(g, "c4_large", PATHS[path], n_slots=4)
+
+
+def test_device_generator_matches_host(g):
+    import torch
+    from tests.gpu_util import to_host
+    primes = synth.PRIMES_28
+    B, D0, L, N = 3, 7, 2, 64
+    params = g.gpir_params_create(N, list(primes))
+    t = torch.empty(B * D0 * 2 * L * N, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(t, t.numel(), 0, 11, synth.TAG_CT, params, N)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t).reshape(B, D0, 2, L, N), synth.ct_tensor(11, B, D0, L, N, primes))
+    # offset start (chunked generation)
+    t2 = torch.empty(100, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(t2, 100, 500, 11, synth.TAG_CT, params, N)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(t2), synth.ct_tensor(11, B, D0, L, N, primes).ravel()[500:600])
+    g.gpir_params_destroy(params)
+
+
+def test_host_entry_point_matches_device(g):
+    import torch
+    from tests.gpu_util import DbHandle, to_dev, to_host, make_problem
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 4, 37, 21, 2, 128
+    ct, db = make_problem(31, B, D0, D1, L, N, primes)
+    want = oracle.rowsel(ct, db, list(primes))
+    h = DbHandle(g, db, N, primes, path_mask=1, on_device=False)
+    try:
+        out = np.zeros((B, D1, 2, L, N), dtype=np.uint32)
+        g.gpir_rowsel_batch_host(h.h, B, np.ascontiguousarray(ct), out, 1)
+        g.gpir_sync(None, 20000)
+        assert np.array_equal(out, want)
+        # twice in a row, larger batch grows the workspace
+        ct2, _ = make_problem(32, 2 * B, D0, D1, L, N, primes)
+        out2 = np.zeros((2 * B, D1, 2, L, N), dtype=np.uint32)
+        g.gpir_rowsel_batch_host(h.h, 2 * B, np.ascontiguousarray(ct2), out2, 1)
+        g.gpir_sync(None, 20000)
+        assert np.array_equal(out2, oracle.rowsel(ct2, db, list(primes)))
+    finally:
+        h.close()
+
+
+def test_upload_rejects_out_of_range_residue(g):
+    import torch
+    from tests.gpu_util import to_dev
+    primes = synth.PRIMES_28
+    db = synth.db_tensor(3, 4, 4, 2, 32, primes)
+    db[2, 1, 1, 7] = primes[1]          # == q1: not canonical
+    params = g.gpir_params_create(32, list(primes))
+    with pytest.raises(g.GpirError) as ei:
+        g.gpir_db_upload(params, 4, 4, to_dev(db), True, 0)
+    assert ei.value.code == g.GPIR_ERANGE
+    db[2, 1, 1, 7] = primes[0] - 1      # < q0 but it sits in limb 1 where q1 < q0
+    with pytest.raises(g.GpirError) as ei:
+        g.gpir_db_upload(params, 4, 4, to_dev(db), True, 0)
+    assert ei.value.code == g.GPIR_ERANGE
+    g.gpir_params_destroy(params)
+
+
+def test_argument_errors(g):
+    import torch
+    from tests.gpu_util import DbHandle, to_dev, make_problem
+    primes = synth.PRIMES_28
+    ct, db = make_problem(1, 2, 8, 8, 2, 32, primes)
+    h = DbHandle(g, db, 32, primes, path_mask=1)
+    try:
+        ct_d = to_dev(ct)
+        with pytest.raises(g.GpirError) as ei:     # output overlaps input
+            g.gpir_rowsel_batch(h.h, 2, ct_d, ct_d, 1)
+        assert ei.value.code == g.GPIR_EINVAL
+        out = torch.empty(2 * 8 * 2 * 2 * 32, dtype=torch.int32, device="cuda")
+        with pytest.raises(g.GpirError) as ei:     # path not prepared at upload
+            g.gpir_rowsel_batch(h.h, 2, ct_d, out, 4)
+        assert ei.value.code == g.GPIR_ENOTSUP
+        with pytest.raises(g.GpirError) as ei:     # batch 0
+            g.gpir_rowsel_batch(h.h, 0, ct_d, out, 1)
+        assert ei.value.code == g.GPIR_EINVAL
+    finally:
+        h.close()
