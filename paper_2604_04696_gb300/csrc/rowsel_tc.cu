@@ -1,10 +1,551 @@
-// RowSel on tcgen05 tensor cores (placeholder until the kernel lands).
-#include "internal.h"
+// RowSel on the 5th-generation tensor cores (tcgen05, bf16 operands, fp32
+// accumulators in tensor memory), exact.
+//
+// What is computed: the per-point modular GEMM of Sec. 2.3 / Sec. 5.1 of the
+// GPIR paper, out[p][m][n] = sum_k ct[p][m][k] * db[p][k][n] mod q, with
+// p = (limb, slot), m = (client, polynomial), k = DB row, n = DB column.
+//
+// Exactness. Each residue x < 2^28 is written in balanced base-256 digits,
+//     x = d0 + d1 2^8 + d2 2^16 + d3 2^24,  d0,d1,d2 in [-128, 127], d3 in [0, 16]
+// (byte u of x + 0x808080, minus 128 for u < 3). Every digit is exactly a bf16.
+// A digit product has |d e| <= 2^14, so a sum of at most 256 of them has
+// magnitude <= 2^22 < 2^24 and is exact in the fp32 accumulator: every partial
+// sum is an integer representable in fp32, so no rounding can occur. Hence
+// the tensor core computes, exactly, for each digit pair (u, v),
+//     D_uv[m][n] = sum_{k in group} a_u[m][k] * b_v[k][n]        (|D| <= 2^22)
+// and  x*y = sum_{u,v} a_u b_v 2^(8(u+v)), so
+//     out = sum_groups sum_{u,v} D_uv * (2^(8(u+v)) mod q)   (mod q),
+// computed in 64-bit integers in the epilogue. The K dimension is processed in
+// groups of 256 rows, each group accumulating in its own tensor-memory buffer.
+//
+// GEMM shape. One MMA instruction computes all 16 digit pairs at once: the A
+// operand stacks the 4 digits of 32 ciphertext rows (M' = 128 rows, ordered
+// m_hi*32 + u*8 + m_lo with m = 8 m_hi + m_lo), the B operand stacks the 4
+// digits of 64 DB columns (N' = 256 rows, ordered n*4 + v); tcgen05.mma
+// .kind::f16 M=128 N=256 K=16, bf16 in, fp32 out. A TMEM lane quarter then
+// holds 8 rows m with all 4 digits u, so the epilogue sums over u with two
+// warp shuffles and over v within the thread.
+//
+// Data movement. The DB is stored once, at upload, as per-slot digit tiles
+// already in the shared-memory image the MMA reads (K-major, 128-byte
+// swizzle): [slot][n-block][k-chunk] x (256 rows x 64 k) bf16. Per batch, an
+// ingest kernel turns the p-major ciphertexts into the same image for the A
+// operand ([slot][m-block][k-chunk] x (128 rows x 64 k)), reading 8 slots
+// (one 32-byte sector) per row. The persistent GEMM kernel streams both with
+// 1-D bulk copies into a 4-stage mbarrier ring (one producer warp), one thread
+// issues the MMAs, four epilogue warps drain tensor memory (double-buffered
+// accumulators, so draining overlaps the next group's MMAs) and write the
+// canonical residues in the p-major output layout.
+#include <cuda.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
 namespace gpir {
-int rowsel_tc_prepare(gpir_db *, cudaStream_t) { return GPIR_ENOTSUP; }
-int rowsel_tc_num_variants() { return 0; }
-int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
-int rowsel_tc_launch(const gpir_db *, uint32_t, const uint32_t *, uint32_t *, int, cudaStream_t) {
-  return GPIR_ENOTSUP;
+namespace {
+
+constexpr int KCHUNK = 64;             // k per pipeline stage (one 128-byte swizzle row of bf16)
+constexpr int KGROUP_CHUNKS = 4;       // 4 x 64 = 256 rows per exact fp32 group
+constexpr int MROWS = 32;              // ciphertext rows (m) per tile -> 128 digit rows
+constexpr int NCOLS = 64;              // DB columns per tile -> 256 digit rows
+constexpr int A_TILE_BYTES = 128 * KCHUNK * 2;   // 16 KB
+constexpr int B_TILE_BYTES = 256 * KCHUNK * 2;   // 32 KB
+constexpr int STAGES = 4;
+constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
+constexpr int GEMM_THREADS = 192;      // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;    // two 128 x 256 fp32 accumulators
+
+struct TcLimb {
+  uint32_t q;
+  uint32_t pad;
+  uint64_t mu;        // floor(2^64 / q)
+  uint64_t off;       // multiple of q, >= 2^55: makes signed sums non-negative
+  int64_t c[7];       // 2^(8s) mod q
+};
+
+struct TcParams {
+  uint32_t M, d0, d1, L, N;
+  uint32_t mblk, nblk, kch;            // tile counts
+  uint64_t units;                       // slots * mblk * nblk
+  const uint16_t *a_tiles;              // [slot][mblk][kch] x 16 KB
+  const uint16_t *b_tiles;              // [slot][nblk][kch] x 32 KB
+  uint32_t *out;
+  unsigned int *err;
+  TcLimb limb[GPIR_MAX_LIMBS];
+};
+
+// ---- PTX wrappers (tcgen05 / bulk copy) ------------------------------------
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// kind::f16, D = f32, A = B = bf16, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- digit helpers -----------------------------------------------------------
+
+// bf16 bit pattern of the balanced digit u (0..3) of x (< 2^28).
+__device__ __forceinline__ uint32_t digit_bf16_bits(uint32_t x, int u) {
+  const uint32_t b = x + 0x808080u;
+  const uint32_t byte = (b >> (8 * u)) & 0xFFu;
+  // 2^23 + byte as an fp32 bit pattern, minus (2^23 + 128) (or 2^23 for the top digit)
+  const float f = __int_as_float(0x4B000000 | byte) - (u < 3 ? 8388736.0f : 8388608.0f);
+  return (uint32_t)__float_as_int(f) >> 16;   // exact: |digit| <= 128 fits bf16
+}
+
+// Exact int32 of an fp32 holding an integer of magnitude <= 2^22.
+__device__ __forceinline__ int32_t f2i_exact(uint32_t bits) {
+  return __float_as_int(__int_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+// ---- ingest: p-major ciphertexts -> A-operand digit tiles --------------------
+
+struct IngestParams {
+  uint32_t M, d0, L, N, mblk, kch, groups8;
+  const uint32_t *ct;
+  uint4 *a_tiles;
+};
+
+// One CTA: 8 consecutive slots x one m-block (32 rows) x one k-chunk (64 k).
+__global__ void __launch_bounds__(256) tc_ingest_kernel(const IngestParams p) {
+  extern __shared__ __align__(16) uint4 tiles[];   // [8 slots][128 rows][8 chunks]
+  uint32_t bid = blockIdx.x;
+  const uint32_t g8 = bid % p.groups8;
+  bid /= p.groups8;
+  const uint32_t kc = bid % p.kch;
+  const uint32_t mb = bid / p.kch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = lane & 7, msub = lane >> 3;
+  const uint64_t slot = (uint64_t)g8 * 8 + s;
+  const bool slot_ok = slot < (uint64_t)p.L * p.N;
+  const uint32_t l = slot_ok ? (uint32_t)(slot / p.N) : 0, t = slot_ok ? (uint32_t)(slot % p.N) : 0;
+  for (int task = warp; task < 64; task += 8) {
+    const int m_local = (task >> 3) * 4 + msub;
+    const int k_oct = task & 7;
+    const uint32_t m = mb * MROWS + m_local;
+    const uint32_t c = m >> 1, r = m & 1;
+    uint32_t v[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t k = kc * KCHUNK + k_oct * 8 + kk;
+      v[kk] = (slot_ok && m < p.M && k < p.d0)
+                  ? __ldcs(p.ct + ((((uint64_t)c * p.d0 + k) * 2 + r) * p.L + l) * p.N + t)
+                  : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      uint4 w;
+      w.x = digit_bf16_bits(v[0], u) | (digit_bf16_bits(v[1], u) << 16);
+      w.y = digit_bf16_bits(v[2], u) | (digit_bf16_bits(v[3], u) << 16);
+      w.z = digit_bf16_bits(v[4], u) | (digit_bf16_bits(v[5], u) << 16);
+      w.w = digit_bf16_bits(v[6], u) | (digit_bf16_bits(v[7], u) << 16);
+      const int row = (m_local >> 3) * 32 + u * 8 + (m_local & 7);
+      tiles[s * 1024 + row * 8 + (k_oct ^ (row & 7))] = w;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 8 * 1024; idx += 256) {
+    const int ss = idx >> 10;
+    const uint64_t sl = (uint64_t)g8 * 8 + ss;
+    if (sl >= (uint64_t)p.L * p.N) continue;
+    p.a_tiles[((sl * p.mblk + mb) * p.kch + kc) * 1024 + (idx & 1023)] = tiles[idx];
+  }
+}
+
+// ---- DB packing (once per upload): p-major DB -> B-operand digit tiles -------
+
+struct PackParams {
+  uint32_t d0, d1, L, N, nblk, kch;
+  const uint32_t *db;
+  uint4 *b_tiles;
+};
+
+// One thread per (slot, n-block, k-chunk, digit row, k octet); slots fastest so
+// the reads of the p-major DB are coalesced.
+__global__ void tc_pack_db_kernel(const PackParams p, uint64_t total) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = i;
+    const uint32_t slot = (uint32_t)(x % ((uint64_t)p.L * p.N));
+    x /= (uint64_t)p.L * p.N;
+    const uint32_t k_oct = (uint32_t)(x % 8);
+    x /= 8;
+    const uint32_t row = (uint32_t)(x % 256);
+    x /= 256;
+    const uint32_t kc = (uint32_t)(x % p.kch);
+    const uint32_t nb = (uint32_t)(x / p.kch);
+    const uint32_t n = nb * NCOLS + row / 4, v = row % 4;
+    const uint32_t l = slot / p.N, t = slot % p.N;
+    uint32_t bits[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t k = kc * KCHUNK + k_oct * 8 + kk;
+      const uint32_t val =
+          (n < p.d1 && k < p.d0) ? p.db[(((uint64_t)k * p.d1 + n) * p.L + l) * p.N + t] : 0u;
+      bits[kk] = digit_bf16_bits(val, (int)v);
+    }
+    uint4 w;
+    w.x = bits[0] | (bits[1] << 16);
+    w.y = bits[2] | (bits[3] << 16);
+    w.z = bits[4] | (bits[5] << 16);
+    w.w = bits[6] | (bits[7] << 16);
+    p.b_tiles[(((uint64_t)slot * p.nblk + nb) * p.kch + kc) * 2048 + row * 8 + (k_oct ^ (row & 7))] = w;
+  }
+}
+
+// ---- persistent GEMM ---------------------------------------------------------
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *acc_full = empty + STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const uint32_t kgroups = (p.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
+
+  // A bounded wait that also gives up when another role already gave up.
+  auto wait = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      if (mbar_try_wait(bar, parity)) return true;
+      if ((n & 63u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, code);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0;
+      bool ok = true;
+      for (uint64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        const uint32_t mb = (uint32_t)(u % p.mblk);
+        const uint64_t r = u / p.mblk;
+        const uint32_t nb = (uint32_t)(r % p.nblk);
+        const uint64_t slot = r / p.nblk;
+        const uint8_t *a_src = (const uint8_t *)p.a_tiles + ((slot * p.mblk + mb) * p.kch) * (uint64_t)A_TILE_BYTES;
+        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
+        for (uint32_t kc = 0; kc < p.kch; ++kc) {
+          if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
+          uint8_t *sa = smem + st * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+          bulk_g2s(sa, a_src + (uint64_t)kc * A_TILE_BYTES, A_TILE_BYTES, &full[st]);
+          bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st]);
+          if (++st == STAGES) {
+            st = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // let copies already issued land before the CTA can exit (bounded)
+        for (int s = 0; s < STAGES; ++s) mbar_wait_bounded(&empty[s], ph ^ 1u, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, buf = 0;
+      uint32_t aph[2] = {0, 0};
+      bool ok = true;
+      for (uint64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        for (uint32_t g = 0; g < kgroups && ok; ++g) {
+          if (!(ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) break;
+          tc_fence_after();
+          const uint32_t tmem_d = tmem_base + buf * 256;
+          const uint32_t c0 = g * KGROUP_CHUNKS;
+          const uint32_t c1 = min(p.kch, c0 + KGROUP_CHUNKS);
+          for (uint32_t kc = c0; kc < c1; ++kc) {
+            if (!(ok = wait(&full[st], ph, kErrTmaWait))) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sb = sa + A_TILE_BYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < KCHUNK / 16; ++k16) {
+              mma_bf16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32),
+                       (kc > c0 || k16 > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[st]);      // frees the smem stage once these MMAs have read it
+            if (++st == STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          mma_commit(&acc_full[buf]);    // accumulator group complete
+          aph[buf] ^= 1u;
+          buf ^= 1u;
+        }
+      }
+      if (!ok) {
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&acc_full[b], aph[b], nullptr, 0);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const uint32_t quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+    const int u = lane >> 3, m_lo = lane & 7;
+    const int m_local = quarter * 8 + m_lo;
+    uint32_t buf = 0;
+    uint32_t aph[2] = {0, 0};
+    bool ok = true;
+    for (uint64_t un = blockIdx.x; un < p.units && ok; un += gridDim.x) {
+      const uint32_t mb = (uint32_t)(un % p.mblk);
+      const uint64_t r = un / p.mblk;
+      const uint32_t nb = (uint32_t)(r % p.nblk);
+      const uint64_t slot = r / p.nblk;
+      const uint32_t l = (uint32_t)(slot / p.N), t = (uint32_t)(slot % p.N);
+      const TcLimb &lm = p.limb[l];
+      const int64_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
+      uint32_t res[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) res[i] = 0;
+      for (uint32_t g = 0; g < kgroups; ++g) {
+        if (!(ok = wait(&acc_full[buf], aph[buf], kErrMmaWait))) break;
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((quarter * 32u) << 16) + buf * 256;
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+          uint32_t d[32];
+          tmem_ld32(taddr + j * 32, d);
+#pragma unroll
+          for (int n8 = 0; n8 < 8; ++n8) {
+            int64_t s = (int64_t)f2i_exact(d[n8 * 4 + 0]) * c0 + (int64_t)f2i_exact(d[n8 * 4 + 1]) * c1 +
+                        (int64_t)f2i_exact(d[n8 * 4 + 2]) * c2 + (int64_t)f2i_exact(d[n8 * 4 + 3]) * c3;
+            s += __shfl_xor_sync(0xffffffffu, s, 8);
+            s += __shfl_xor_sync(0xffffffffu, s, 16);
+            if ((n8 & 3) == u) {
+              const uint32_t rr = reduce64((uint64_t)(s + (int64_t)lm.off), lm.q, lm.mu);
+              uint32_t &acc = res[j * 2 + (n8 >> 2)];
+              acc += rr;
+              acc = acc >= lm.q ? acc - lm.q : acc;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        aph[buf] ^= 1u;
+        buf ^= 1u;
+      }
+      if (!ok) break;
+      const uint32_t m = mb * MROWS + m_local;
+      if (m < p.M) {
+        const uint32_t c = m >> 1, rr = m & 1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t n = nb * NCOLS + j * 8 + h * 4 + u;
+            if (n < p.d1) p.out[((((uint64_t)c * p.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+static TcLimb make_limb(uint32_t q) {
+  TcLimb t;
+  t.q = q;
+  t.pad = 0;
+  t.mu = ~0ull / q;
+  const uint64_t two55 = 1ull << 55;
+  t.off = ((two55 + q - 1) / q) * (uint64_t)q;
+  uint64_t pw = 1;
+  for (int s = 0; s < 7; ++s) {
+    t.c[s] = (int64_t)(pw % q);
+    pw = (pw << 8) % q;
+  }
+  return t;
+}
+
+}  // namespace
+
+int rowsel_tc_num_variants() { return 1; }
+int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
+
+int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
+  const uint32_t L = db->params.num_limbs, N = db->params.n;
+  const uint32_t nblk = (db->d1 + NCOLS - 1) / NCOLS, kch = (db->d0 + KCHUNK - 1) / KCHUNK;
+  const uint64_t slots = (uint64_t)L * N;
+  const size_t bytes = (size_t)slots * nblk * kch * B_TILE_BYTES;
+  cudaError_t e = cudaMalloc(&db->db_digits, bytes);
+  if (e != cudaSuccess) {
+    db->db_digits = nullptr;
+    return set_cuda_error(e);
+  }
+  db->db_digits_bytes = bytes;
+  PackParams pp;
+  pp.d0 = db->d0;
+  pp.d1 = db->d1;
+  pp.L = L;
+  pp.N = N;
+  pp.nblk = nblk;
+  pp.kch = kch;
+  pp.db = db->db_pmajor;
+  pp.b_tiles = reinterpret_cast<uint4 *>(db->db_digits);
+  const uint64_t total = slots * nblk * kch * 256 * 8;
+  tc_pack_db_kernel<<<sm_count() * 16, 256, 0, stream>>>(pp, total);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  e = cudaStreamSynchronize(stream);
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
+                     cudaStream_t stream) {
+  (void)variant;
+  gpir_db *db = const_cast<gpir_db *>(db_c);
+  if (!db->db_digits) return GPIR_ENOTSUP;
+  const uint32_t L = db->params.num_limbs, N = db->params.n, M = 2 * batch;
+  const uint32_t mblk = (M + MROWS - 1) / MROWS, nblk = (db->d1 + NCOLS - 1) / NCOLS;
+  const uint32_t kch = (db->d0 + KCHUNK - 1) / KCHUNK;
+  const uint64_t slots = (uint64_t)L * N;
+  const size_t a_bytes = (size_t)slots * mblk * kch * A_TILE_BYTES;
+  if (db->tc_ws_bytes < a_bytes) {
+    if (db->tc_ws) {
+      cudaStreamSynchronize(stream);
+      cudaFree(db->tc_ws);
+    }
+    db->tc_ws = nullptr;
+    db->tc_ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&db->tc_ws, a_bytes);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    db->tc_ws_bytes = a_bytes;
+  }
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    attr_done = true;
+  }
+  IngestParams ip;
+  ip.M = M;
+  ip.d0 = db->d0;
+  ip.L = L;
+  ip.N = N;
+  ip.mblk = mblk;
+  ip.kch = kch;
+  ip.groups8 = (uint32_t)((slots + 7) / 8);
+  ip.ct = ct;
+  ip.a_tiles = reinterpret_cast<uint4 *>(db->tc_ws);
+  const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
+  if (igrid > 0x7fffffffull) return GPIR_EINVAL;
+  tc_ingest_kernel<<<(unsigned)igrid, 256, 8 * 16384, stream>>>(ip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+
+  TcParams tp;
+  memset(&tp, 0, sizeof(tp));
+  tp.M = M;
+  tp.d0 = db->d0;
+  tp.d1 = db->d1;
+  tp.L = L;
+  tp.N = N;
+  tp.mblk = mblk;
+  tp.nblk = nblk;
+  tp.kch = kch;
+  tp.units = slots * mblk * nblk;
+  tp.a_tiles = reinterpret_cast<const uint16_t *>(db->tc_ws);
+  tp.b_tiles = db->db_digits;
+  tp.out = out;
+  tp.err = device_error_word();
+  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(db->params.primes[l]);
+  const int grid = (int)std::min<uint64_t>((uint64_t)sm_count(), tp.units);
+  tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, stream>>>(tp);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
 }  // namespace gpir

@@ -10,7 +10,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-PATHS = {"cudacore": 1}
+PATHS = {"cudacore": 1, "imma": 2, "tc": 4}
+PATH_LIST = ["cudacore", "imma", "tc"]
 
 
 @pytest.fixture(scope="module")
@@ -23,8 +24,14 @@ def _avail_paths(g):
     return [name for name, p in PATHS.items() if g.gpir_num_variants(p) > 0]
 
 
+def _skip_unbuilt(g, path):
+    if g.gpir_num_variants(path) == 0:
+        pytest.skip("path not built")
+
+
 def _check_full(g, B, D0, D1, L, N, primes, seed, path, variants=None):
     from tests.gpu_util import DbHandle, to_dev, to_host, make_problem
+    _skip_unbuilt(g, path)
     ct, db = make_problem(seed, B, D0, D1, L, N, primes)
     want = oracle.rowsel(ct, db, list(primes))
     h = DbHandle(g, db, N, primes, path_mask=path)
@@ -54,7 +61,7 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "B%d_D0%d_D1%d_L%d_N%d" % s[:5])
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_rowsel_vs_oracle(g, shape, path):
     B, D0, D1, L, N, primes = shape
     seed = 0 if (B, D0, D1, N) == (1, 16, 16, 2048) else 1000 + B + D0
@@ -63,17 +70,18 @@ def test_rowsel_vs_oracle(g, shape, path):
     _check_full(g, B, D0, D1, L, N, primes, seed, PATHS[path])
 
 
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_every_variant(g, path):
     p = PATHS[path]
     nv = g.gpir_num_variants(p)
     _check_full(g, 6, 70, 40, 2, 64, synth.PRIMES_28, 77, p, variants=list(range(nv)))
 
 
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_worst_case_accumulation(g, path):
     """All residues q-1 with D0 = 2048: every product is maximal; result D0 mod q."""
     from tests.gpu_util import DbHandle, to_dev, to_host
+    _skip_unbuilt(g, PATHS[path])
     primes = synth.PRIMES_28
     B, D0, D1, L, N = 2, 2048, 8, 2, 32
     ct = np.empty((B, D0, 2, L, N), dtype=np.uint32)
@@ -90,9 +98,10 @@ def test_worst_case_accumulation(g, path):
         assert np.all(got[:, :, :, l] == D0 % q)
 
 
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_one_hot_returns_row(g, path):
     from tests.gpu_util import DbHandle, to_dev, to_host
+    _skip_unbuilt(g, PATHS[path])
     primes = synth.PRIMES_28
     B, D0, D1, L, N = 4, 50, 12, 2, 256
     db = synth.db_tensor(5, D0, D1, L, N, primes)
@@ -114,6 +123,7 @@ def _sampled_full_size(g, name, path, n_slots=6):
     """Full-size workload generated on the device; oracle on sampled slots."""
     import torch
     from tests.gpu_util import to_host
+    _skip_unbuilt(g, path)
     cfg = synth.config_shapes(name)
     N, L, D0, D1, seed, primes = cfg["N"], cfg["L"], cfg["D0"], cfg["D1"], cfg["seed"], cfg["primes"]
     B = cfg["B"] if isinstance(cfg["B"], int) else max(cfg["B"])
@@ -144,12 +154,12 @@ def _sampled_full_size(g, name, path, n_slots=6):
         g.gpir_params_destroy(params)
 
 
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_full_size_rowsel_32_clients_sampled(g, path):
     _sampled_full_size(g, "c2_rowsel", PATHS[path])
 
 
-@pytest.mark.parametrize("path", ["cudacore"])
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_full_size_large_db_sampled(g, path):
     _sampled_full_size(g, "c4_large", PATHS[path], n_slots=4)
 
