@@ -46,6 +46,7 @@ extern "C" {
 #define GPIR_ECUDA      -4  /* a CUDA runtime call failed                   */
 #define GPIR_ETIMEOUT   -5  /* a bounded wait (host or device) expired      */
 #define GPIR_ENOTSUP    -6  /* path not prepared for this database / device */
+#define GPIR_ETOOBIG    -7  /* problem needs more than a fixed-size buffer  */
 
 /* ---- compute paths (also usable as a bit mask at upload) ---------------- */
 #define GPIR_PATH_AUTO      0  /* fastest prepared path for the shape        */
@@ -154,6 +155,32 @@ int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant)
 int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_t seed,
                       uint64_t tag, const gpir_params_t *params, uint64_t inner,
                       void *stream);
+
+/* Allocation-free RowSel (no counterpart in the paper: an interface for
+ * callers that cannot allocate device memory while they run, such as code
+ * running under a CUDA stream capture, or services whose device-memory budget
+ * is fixed at start-up and that must not call the allocator on their request
+ * path). Same result as gpir_rowsel_batch(db, batch, ct_dev, out_dev,
+ * GPIR_PATH_TC, stream), but the tensor-core path's per-batch digit-tile
+ * workspace lives in a fixed device array of GPIR_NOALLOC_SCRATCH_BYTES
+ * compiled into the library instead of memory from cudaMalloc; the call
+ * allocates nothing. The caller passes the input and output buffers as usual.
+ *  - The workspace needed is L*N * ceil(2*batch/32) * ceil(D0/64) * 16 KiB;
+ *    larger problems are rejected with GPIR_ETOOBIG before anything is
+ *    enqueued.
+ *  - The database must have been uploaded with the GPIR_PATH_TC bit
+ *    (GPIR_ENOTSUP otherwise) on the current device.
+ *  - The first call on each device looks up the array's device address and
+ *    sets kernel attributes (no allocation); make that first call before any
+ *    stream capture that will contain later calls.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose work overlaps on the GPU (different streams, or different
+ *    host threads) race on it and must be serialized by the caller.
+ *  - Every device that loads the library holds the array until the process
+ *    exits. Asynchronous on `stream`. */
+#define GPIR_NOALLOC_SCRATCH_BYTES (64u << 20)
+int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
+                              uint32_t *out_dev, void *stream);
 
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return

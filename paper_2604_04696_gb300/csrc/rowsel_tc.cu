@@ -41,6 +41,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -549,3 +550,114 @@ int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, ui
 }
 
 }  // namespace gpir
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point (gpir_rowsel_batch_noalloc).
+//
+// Some callers cannot call cudaMalloc while they run RowSel: code executing
+// under a CUDA stream capture, services that must not touch the device
+// allocator after start-up (memory budgets fixed in advance, allocator locks
+// on a latency-critical path), or hosts whose allocator is owned by another
+// runtime. For them this entry point runs the tensor-core path with its
+// per-batch digit-tile workspace placed in the fixed device array below
+// instead of memory from cudaMalloc. The array lives as long as the library
+// is loaded on a device (every device that loads the library holds it), holds
+// GPIR_NOALLOC_SCRATCH_BYTES, and is shared by all calls: calls that overlap
+// on the GPU (several streams, several host threads) race on it.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) uint8_t g_noalloc_tiles[GPIR_NOALLOC_SCRATCH_BYTES];
+
+namespace gpir {
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices];   // device address of g_noalloc_tiles, per device
+
+// Once per device, with that device current: resolve the array's device
+// address (the name g_noalloc_tiles is only a host-side stand-in) and set the
+// kernels' shared-memory limits. Allocates nothing.
+int noalloc_setup(int dev, void **tiles) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    g_noalloc_addr[dev] = p;
+  }
+  *tiles = g_noalloc_addr[dev];
+  return GPIR_OK;
+}
+
+}  // namespace
+}  // namespace gpir
+
+extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
+                                         uint32_t *out_dev, void *stream) {
+  using namespace gpir;
+  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  if (!(db->path_mask & GPIR_PATH_TC) || !db->db_digits) return GPIR_ENOTSUP;
+  const uint32_t L = db->params.num_limbs, N = db->params.n, M = 2 * batch;
+  const uint64_t slots = (uint64_t)L * N;
+  const size_t ct_bytes = (size_t)batch * db->d0 * 2 * slots * 4;
+  const size_t out_bytes = (size_t)batch * db->d1 * 2 * slots * 4;
+  const uintptr_t a0 = (uintptr_t)ct_dev, a1 = a0 + ct_bytes, b0 = (uintptr_t)out_dev, b1 = b0 + out_bytes;
+  if (a0 < b1 && b0 < a1) return GPIR_EINVAL;
+  const uint32_t mblk = (M + MROWS - 1) / MROWS, nblk = (db->d1 + NCOLS - 1) / NCOLS;
+  const uint32_t kch = (db->d0 + KCHUNK - 1) / KCHUNK;
+  const uint64_t a_bytes = slots * mblk * kch * (uint64_t)A_TILE_BYTES;
+  if (a_bytes > (uint64_t)GPIR_NOALLOC_SCRATCH_BYTES) return GPIR_ETOOBIG;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= kNoallocMaxDevices || dev != db->device) return GPIR_EINVAL;
+  void *tiles = nullptr;
+  int rc = noalloc_setup(dev, &tiles);
+  if (rc != GPIR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  IngestParams ip;
+  ip.M = M;
+  ip.d0 = db->d0;
+  ip.L = L;
+  ip.N = N;
+  ip.mblk = mblk;
+  ip.kch = kch;
+  ip.groups8 = (uint32_t)((slots + 7) / 8);
+  ip.ct = ct_dev;
+  ip.a_tiles = reinterpret_cast<uint4 *>(tiles);
+  const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
+  if (igrid > 0x7fffffffull) return GPIR_EINVAL;
+  tc_ingest_kernel<<<(unsigned)igrid, 256, 8 * 16384, s>>>(ip);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+
+  TcParams tp;
+  memset(&tp, 0, sizeof(tp));
+  tp.M = M;
+  tp.d0 = db->d0;
+  tp.d1 = db->d1;
+  tp.L = L;
+  tp.N = N;
+  tp.mblk = mblk;
+  tp.nblk = nblk;
+  tp.kch = kch;
+  tp.units = slots * mblk * nblk;
+  tp.a_tiles = reinterpret_cast<const uint16_t *>(tiles);
+  tp.b_tiles = db->db_digits;
+  tp.out = out_dev;
+  tp.err = device_error_word();
+  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(db->params.primes[l]);
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int grid = (int)std::min<uint64_t>((uint64_t)sms, tp.units);
+  tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(tp);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}

@@ -19,6 +19,8 @@ GPIR_ENOMEM = -3
 GPIR_ECUDA = -4
 GPIR_ETIMEOUT = -5
 GPIR_ENOTSUP = -6
+GPIR_ETOOBIG = -7
+GPIR_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 GPIR_PATH_AUTO = 0
 GPIR_PATH_CUDACORE = 1
@@ -58,6 +60,7 @@ def _load():
         "gpir_rowsel_batch": (I, [P, U32, P, P, I, P]),
         "gpir_rowsel_batch_host": (I, [P, U32, P, P, I, P]),
         "gpir_rowsel_multi": (I, [ctypes.POINTER(gpir_job_t), U32, I, P]),
+        "gpir_rowsel_batch_noalloc": (I, [P, U32, P, P, P]),
         "gpir_sync": (I, [P, U32]),
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
@@ -146,6 +149,12 @@ def gpir_rowsel_batch(db, batch, ct_dev, out_dev, path=GPIR_PATH_AUTO, stream=No
 def gpir_rowsel_batch_host(db, batch, ct_host, out_host, path=GPIR_PATH_AUTO, stream=None):
     return _check(lib.gpir_rowsel_batch_host(db, int(batch), _ptr(ct_host), _ptr(out_host), int(path),
                                              _stream(stream)), "gpir_rowsel_batch_host")
+
+
+def gpir_rowsel_batch_noalloc(db, batch, ct_dev, out_dev, stream=None):
+    """Tensor-core RowSel with no device allocation (fixed internal workspace)."""
+    return _check(lib.gpir_rowsel_batch_noalloc(db, int(batch), _ptr(ct_dev), _ptr(out_dev), _stream(stream)),
+                  "gpir_rowsel_batch_noalloc")
 
 
 def gpir_rowsel_multi(jobs, path=GPIR_PATH_AUTO, stream=None):
