@@ -33,7 +33,7 @@
 // operand ([slot][m-block][k-chunk] x (128 rows x 64 k)), reading 8 slots
 // (one 32-byte sector) per row. The persistent GEMM kernel streams both with
 // 1-D bulk copies into a 4-stage mbarrier ring (one producer warp), one thread
-// issues the MMAs, four epilogue warps drain tensor memory (double-buffered
+// issues the MMAs, sixteen epilogue warps drain tensor memory (double-buffered
 // accumulators, so draining overlaps the next group's MMAs) and write the
 // canonical residues in the p-major output layout.
 #include <cuda.h>
@@ -56,7 +56,8 @@ constexpr int A_TILE_BYTES = 128 * KCHUNK * 2;   // 16 KB
 constexpr int B_TILE_BYTES = 256 * KCHUNK * 2;   // 32 KB
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
-constexpr int GEMM_THREADS = 192;      // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int EPI_WARPS = 16;          // 4 per TMEM lane quarter, 2 column chunks each
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;   // warp 0 producer, warp 1 MMA, then epilogue
 constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;    // two 128 x 256 fp32 accumulators
 
@@ -65,7 +66,7 @@ struct TcLimb {
   uint32_t pad;
   uint64_t mu;        // floor(2^64 / q)
   uint64_t off;       // multiple of q, >= 2^55: makes signed sums non-negative
-  int64_t c[7];       // 2^(8s) mod q
+  int32_t c[8];       // 2^(8s) mod q, s = 0..6 (c[7] unused)
 };
 
 struct TcParams {
@@ -140,11 +141,6 @@ __device__ __forceinline__ uint32_t digit_bf16_bits(uint32_t x, int u) {
   return (uint32_t)__float_as_int(f) >> 16;   // exact: |digit| <= 128 fits bf16
 }
 
-// Exact int32 of an fp32 holding an integer of magnitude <= 2^22.
-__device__ __forceinline__ int32_t f2i_exact(uint32_t bits) {
-  return __float_as_int(__int_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
-
 // ---- ingest: p-major ciphertexts -> A-operand digit tiles --------------------
 
 struct IngestParams {
@@ -154,8 +150,14 @@ struct IngestParams {
 };
 
 // One CTA: 8 consecutive slots x one m-block (32 rows) x one k-chunk (64 k).
-__global__ void __launch_bounds__(256) tc_ingest_kernel(const IngestParams p) {
-  extern __shared__ __align__(16) uint4 tiles[];   // [8 slots][128 rows][8 chunks]
+// Each slot's 16 KB tile is staged in shared memory with a 16-byte pad after
+// it, so the 8 lanes of a store phase (8 different slots) hit 8 different
+// bank groups.
+constexpr int INGEST_THREADS = 512;
+constexpr int TILE_PAD = 1025;                       // uint4 per staged tile incl. pad
+constexpr size_t INGEST_SMEM = 8 * TILE_PAD * 16;
+__global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestParams p) {
+  extern __shared__ __align__(16) uint4 tiles[];   // [8 slots][128 rows x 8 chunks + pad]
   uint32_t bid = blockIdx.x;
   const uint32_t g8 = bid % p.groups8;
   bid /= p.groups8;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) tc_ingest_kernel(const IngestParams p) {
   const uint64_t slot = (uint64_t)g8 * 8 + s;
   const bool slot_ok = slot < (uint64_t)p.L * p.N;
   const uint32_t l = slot_ok ? (uint32_t)(slot / p.N) : 0, t = slot_ok ? (uint32_t)(slot % p.N) : 0;
-  for (int task = warp; task < 64; task += 8) {
+  for (int task = warp; task < 64; task += INGEST_THREADS / 32) {
     const int m_local = (task >> 3) * 4 + msub;
     const int k_oct = task & 7;
     const uint32_t m = mb * MROWS + m_local;
@@ -187,15 +189,15 @@ __global__ void __launch_bounds__(256) tc_ingest_kernel(const IngestParams p) {
       w.z = digit_bf16_bits(v[4], u) | (digit_bf16_bits(v[5], u) << 16);
       w.w = digit_bf16_bits(v[6], u) | (digit_bf16_bits(v[7], u) << 16);
       const int row = (m_local >> 3) * 32 + u * 8 + (m_local & 7);
-      tiles[s * 1024 + row * 8 + (k_oct ^ (row & 7))] = w;
+      tiles[s * TILE_PAD + row * 8 + (k_oct ^ (row & 7))] = w;
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 8 * 1024; idx += 256) {
+  for (int idx = threadIdx.x; idx < 8 * 1024; idx += INGEST_THREADS) {
     const int ss = idx >> 10;
     const uint64_t sl = (uint64_t)g8 * 8 + ss;
     if (sl >= (uint64_t)p.L * p.N) continue;
-    p.a_tiles[((sl * p.mblk + mb) * p.kch + kc) * 1024 + (idx & 1023)] = tiles[idx];
+    p.a_tiles[((sl * p.mblk + mb) * p.kch + kc) * 1024 + (idx & 1023)] = tiles[ss * TILE_PAD + (idx & 1023)];
   }
 }
 
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], EPI_WARPS);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -364,8 +366,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const uint32_t quarter = warp & 3;                 // TMEM lanes 32*quarter .. +31
+    // ---------------- epilogue (warps 2 .. 2+EPI_WARPS-1) ----------------
+    // Warp w reads TMEM lane quarter w % 4 (hardware rule); the four warps of
+    // a quarter split the 8 column chunks of the 256-column accumulator.
+    constexpr int CHUNKS = 8 / (EPI_WARPS / 4);
+    const uint32_t quarter = warp & 3;
+    const int jbase = ((warp - 2) >> 2) * CHUNKS;
     const int u = lane >> 3, m_lo = lane & 7;
     const int m_local = quarter * 8 + m_lo;
     uint32_t buf = 0;
@@ -378,26 +384,32 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       const uint64_t slot = r / p.nblk;
       const uint32_t l = (uint32_t)(slot / p.N), t = (uint32_t)(slot % p.N);
       const TcLimb &lm = p.limb[l];
-      const int64_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
-      uint32_t res[16];
+      const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
+      // fp32 D + 1.5*2^23 has bit pattern 0x4B400000 + D for |D| <= 2^22, so
+      // sum_v bits_v * c_v - 0x4B400000 * sum_v c_v = sum_v D_v * c_v exactly.
+      const int64_t kfix = (int64_t)0x4B400000 * ((int64_t)c0 + c1 + c2 + c3);
+      uint32_t res[2 * CHUNKS];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) res[i] = 0;
+      for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
       for (uint32_t g = 0; g < kgroups; ++g) {
         if (!(ok = wait(&acc_full[buf], aph[buf], kErrMmaWait))) break;
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((quarter * 32u) << 16) + buf * 256;
-#pragma unroll 1
-        for (int j = 0; j < 8; ++j) {
+        const uint32_t taddr = tmem_base + ((quarter * 32u) << 16) + buf * 256 + jbase * 32;
+#pragma unroll
+        for (int j = 0; j < CHUNKS; ++j) {
           uint32_t d[32];
           tmem_ld32(taddr + j * 32, d);
 #pragma unroll
           for (int n8 = 0; n8 < 8; ++n8) {
-            int64_t s = (int64_t)f2i_exact(d[n8 * 4 + 0]) * c0 + (int64_t)f2i_exact(d[n8 * 4 + 1]) * c1 +
-                        (int64_t)f2i_exact(d[n8 * 4 + 2]) * c2 + (int64_t)f2i_exact(d[n8 * 4 + 3]) * c3;
-            s += __shfl_xor_sync(0xffffffffu, s, 8);
-            s += __shfl_xor_sync(0xffffffffu, s, 16);
+            const int32_t b0 = __float_as_int(__uint_as_float(d[n8 * 4 + 0]) + 12582912.0f);
+            const int32_t b1 = __float_as_int(__uint_as_float(d[n8 * 4 + 1]) + 12582912.0f);
+            const int32_t b2 = __float_as_int(__uint_as_float(d[n8 * 4 + 2]) + 12582912.0f);
+            const int32_t b3 = __float_as_int(__uint_as_float(d[n8 * 4 + 3]) + 12582912.0f);
+            int64_t sv = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3 - kfix;
+            sv += __shfl_xor_sync(0xffffffffu, sv, 8);
+            sv += __shfl_xor_sync(0xffffffffu, sv, 16);
             if ((n8 & 3) == u) {
-              const uint32_t rr = reduce64((uint64_t)(s + (int64_t)lm.off), lm.q, lm.mu);
+              const uint32_t rr = reduce64((uint64_t)(sv + (int64_t)lm.off), lm.q, lm.mu);
               uint32_t &acc = res[j * 2 + (n8 >> 2)];
               acc += rr;
               acc = acc >= lm.q ? acc - lm.q : acc;
@@ -415,10 +427,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       if (m < p.M) {
         const uint32_t c = m >> 1, rr = m & 1;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < CHUNKS; ++j) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const uint32_t n = nb * NCOLS + j * 8 + h * 4 + u;
+            const uint32_t n = nb * NCOLS + (jbase + j) * 8 + h * 4 + u;
             if (n < p.d1) p.out[((((uint64_t)c * p.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
           }
         }
@@ -443,9 +455,10 @@ static TcLimb make_limb(uint32_t q) {
   t.off = ((two55 + q - 1) / q) * (uint64_t)q;
   uint64_t pw = 1;
   for (int s = 0; s < 7; ++s) {
-    t.c[s] = (int64_t)(pw % q);
+    t.c[s] = (int32_t)(pw % q);
     pw = (pw << 8) % q;
   }
+  t.c[7] = 0;
   return t;
 }
 
@@ -507,7 +520,7 @@ int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, ui
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
+      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INGEST_SMEM);
     if (e != cudaSuccess) return set_cuda_error(e);
     attr_done = true;
   }
@@ -523,7 +536,7 @@ int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, ui
   ip.a_tiles = reinterpret_cast<uint4 *>(db->tc_ws);
   const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
   if (igrid > 0x7fffffffull) return GPIR_EINVAL;
-  tc_ingest_kernel<<<(unsigned)igrid, 256, 8 * 16384, stream>>>(ip);
+  tc_ingest_kernel<<<(unsigned)igrid, INGEST_THREADS, INGEST_SMEM, stream>>>(ip);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e);
 
@@ -586,7 +599,7 @@ int noalloc_setup(int dev, void **tiles) {
     if (e != cudaSuccess) return set_cuda_error(e);
     e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
+      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INGEST_SMEM);
     if (e != cudaSuccess) return set_cuda_error(e);
     g_noalloc_addr[dev] = p;
   }
@@ -633,7 +646,7 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
   ip.a_tiles = reinterpret_cast<uint4 *>(tiles);
   const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
   if (igrid > 0x7fffffffull) return GPIR_EINVAL;
-  tc_ingest_kernel<<<(unsigned)igrid, 256, 8 * 16384, s>>>(ip);
+  tc_ingest_kernel<<<(unsigned)igrid, INGEST_THREADS, INGEST_SMEM, s>>>(ip);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e);
 
