@@ -119,12 +119,30 @@ int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_de
 int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_host,
                            uint32_t *out_host, int path, void *stream);
 
-/* Several RowSel problems (possibly different databases, uneven D0 / D1 and
- * batch sizes) in ONE persistent launch: work tiles of all jobs are numbered
- * into one global index space and claimed by resident CTAs from a device
- * counter. All jobs must share the same params (N, L, primes). Asynchronous.
- * The launch is capturable in a CUDA graph. */
+/* Several RowSel problems at once (Sec. 5.1.1's batched GEMMs over a list of
+ * jobs): different databases, uneven D0 / D1 and batch sizes. On the
+ * tensor-core path the work units of up to 8 jobs are numbered into one
+ * index space and processed by ONE persistent launch (one CTA per SM, units
+ * taken round-robin by CTA index), after one ingest launch; larger lists use
+ * one such pair per 8 jobs. CUDA-core and IMMA paths use one launch per job.
+ * GPIR_PATH_AUTO picks the tensor-core path when every job's database has
+ * it. All jobs must share the same params (N, L, primes) and every job's
+ * ct / out must not overlap any other buffer of the call. The tensor-core
+ * workspace for the call is grown on demand (not while the stream is being
+ * captured: GPIR_ENOMEM then). Asynchronous. */
 int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream);
+
+/* CUDA-graph plan of one gpir_rowsel_multi call (the paper replays its
+ * fine-grained launches from CUDA graphs, Sec. 5.2.2). Create runs the call
+ * once eagerly on `stream` (sizing workspaces; synchronizes), then captures
+ * it; launch replays it on any stream. The job list (buffers, batch sizes)
+ * is fixed at creation: refill the same ct buffers and replay. `stream` must
+ * not be the legacy default stream. */
+typedef struct gpir_graph gpir_graph_t;
+int gpir_graph_create(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream,
+                      gpir_graph_t **out);
+int gpir_graph_launch(gpir_graph_t *graph, void *stream);
+int gpir_graph_destroy(gpir_graph_t *graph);
 
 /* Wait for `stream` for at most timeout_ms milliseconds (0 = no limit).
  * GPIR_ETIMEOUT if the stream is still busy, or if a kernel of this library

@@ -133,7 +133,7 @@ static bool is_prime_u32(uint32_t n) {
   return true;
 }
 
-static int pick_variant(const gpir_db *db, uint32_t batch, int path) {
+int pick_variant(const gpir_db *db, uint32_t batch, int path) {
   {
     std::lock_guard<std::mutex> lk(*db->mu);
     auto it = db->variants->find({path, batch});

@@ -93,6 +93,12 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
 int rowsel_tc_num_variants();
 int rowsel_tc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
 
+int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
+size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs);
+
 int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaStream_t stream);
+int dispatch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int path, int variant,
+             cudaStream_t s);
+int pick_variant(const gpir_db *db, uint32_t batch, int path);
 
 }  // namespace gpir

@@ -1,15 +1,97 @@
-// Multi-job RowSel (placeholder: one launch per job).
+// Several RowSel problems in one call (batching across clients and resident
+// databases of uneven D0 / D1, Sec. 5.1.1's batched GEMMs generalised to a
+// job list), and CUDA-graph plans of such calls.
+//
+// Tensor-core path: all jobs' work units are numbered into one index space
+// and processed by ONE persistent GEMM launch (after one ingest launch), up
+// to 8 jobs per launch. CUDA-core and IMMA paths: one launch per job.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
 #include "internal.h"
+
 namespace gpir {
-int dispatch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int path, int variant,
-             cudaStream_t s);
+
 int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaStream_t stream) {
+  int p = path;
+  if (p == GPIR_PATH_AUTO) {
+    bool all_tc = true;
+    for (uint32_t k = 0; k < njobs; ++k) all_tc = all_tc && (jobs[k].db->path_mask & GPIR_PATH_TC);
+    p = all_tc ? GPIR_PATH_TC : GPIR_PATH_CUDACORE;
+  }
+  for (uint32_t k = 0; k < njobs; ++k)
+    if (!(jobs[k].db->path_mask & p)) return GPIR_ENOTSUP;
+  if (p == GPIR_PATH_TC) return rowsel_tc_multi(jobs, njobs, stream);
   for (uint32_t k = 0; k < njobs; ++k) {
-    int p = path == GPIR_PATH_AUTO ? GPIR_PATH_CUDACORE : path;
     int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, p,
-                      rowsel_cc_default_variant(jobs[k].batch, jobs[k].db->d0, jobs[k].db->d1), stream);
+                      pick_variant(jobs[k].db, jobs[k].batch, p), stream);
     if (rc) return rc;
   }
   return GPIR_OK;
 }
+
 }  // namespace gpir
+
+struct gpir_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+using namespace gpir;
+
+extern "C" {
+
+int gpir_graph_create(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream, gpir_graph_t **out) {
+  if (!jobs || njobs == 0 || !out || !stream) return GPIR_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  // One eager run sizes every workspace outside the capture (and checks the
+  // arguments); its results are overwritten by every replay.
+  int rc = gpir_rowsel_multi(jobs, njobs, path, stream);
+  if (rc != GPIR_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  gpir_graph *g = new (std::nothrow) gpir_graph;
+  if (!g) return GPIR_ENOMEM;
+  g->graph = nullptr;
+  g->exec = nullptr;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    delete g;
+    return set_cuda_error(e);
+  }
+  rc = gpir_rowsel_multi(jobs, njobs, path, stream);
+  e = cudaStreamEndCapture(s, &g->graph);
+  if (rc != GPIR_OK || e != cudaSuccess) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return rc != GPIR_OK ? rc : set_cuda_error(e);
+  }
+  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return set_cuda_error(e);
+  }
+  *out = g;
+  return GPIR_OK;
+}
+
+int gpir_graph_launch(gpir_graph_t *g, void *stream) {
+  if (!g) return GPIR_EINVAL;
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+int gpir_graph_destroy(gpir_graph_t *g) {
+  if (!g) return GPIR_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return GPIR_OK;
+}
+
+}  // extern "C"

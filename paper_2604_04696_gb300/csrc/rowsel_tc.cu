@@ -69,16 +69,45 @@ struct TcLimb {
   int32_t c[8];       // 2^(8s) mod q, s = 0..6 (c[7] unused)
 };
 
-struct TcParams {
-  uint32_t M, d0, d1, L, N;
-  uint32_t mblk, nblk, kch;            // tile counts
-  uint64_t units;                       // slots * mblk * nblk
+constexpr int MAX_JOBS = 8;            // RowSel problems per launch (inline job table)
+
+// One RowSel problem of a launch. Units of all jobs are numbered into one
+// index space [0, units): job j owns [unit_begin, unit_begin + slots*mblk*nblk),
+// ordered m-block fastest, then n-block, then slot.
+struct TcJob {
   const uint16_t *a_tiles;              // [slot][mblk][kch] x 16 KB
   const uint16_t *b_tiles;              // [slot][nblk][kch] x 32 KB
   uint32_t *out;
+  uint32_t M, d0, d1, mblk, nblk, kch;
+  uint64_t unit_begin;
+};
+
+struct TcParams {
+  uint32_t L, N, njobs, pad;
+  uint64_t units;
   unsigned int *err;
+  TcJob job[MAX_JOBS];
   TcLimb limb[GPIR_MAX_LIMBS];
 };
+
+struct UnitRef {
+  uint32_t j, mb, nb;
+  uint64_t slot;
+};
+
+__device__ __forceinline__ UnitRef decode_unit(const TcParams &p, uint64_t u) {
+  uint32_t j = 0;
+  while (j + 1 < p.njobs && u >= p.job[j + 1].unit_begin) ++j;
+  const TcJob &jb = p.job[j];
+  uint64_t x = u - jb.unit_begin;
+  UnitRef r;
+  r.j = j;
+  r.mb = (uint32_t)(x % jb.mblk);
+  x /= jb.mblk;
+  r.nb = (uint32_t)(x % jb.nblk);
+  r.slot = x / jb.nblk;
+  return r;
+}
 
 // ---- PTX wrappers (tcgen05 / bulk copy) ------------------------------------
 
@@ -143,10 +172,16 @@ __device__ __forceinline__ uint32_t digit_bf16_bits(uint32_t x, int u) {
 
 // ---- ingest: p-major ciphertexts -> A-operand digit tiles --------------------
 
-struct IngestParams {
-  uint32_t M, d0, L, N, mblk, kch, groups8;
+struct IngestJob {
   const uint32_t *ct;
   uint4 *a_tiles;
+  uint32_t M, d0, mblk, kch;
+  uint32_t block_begin;                 // first CTA of this job
+};
+
+struct IngestParams {
+  uint32_t L, N, groups8, njobs;
+  IngestJob job[MAX_JOBS];
 };
 
 // One CTA: 8 consecutive slots x one m-block (32 rows) x one k-chunk (64 k).
@@ -158,11 +193,14 @@ constexpr int TILE_PAD = 1025;                       // uint4 per staged tile in
 constexpr size_t INGEST_SMEM = 8 * TILE_PAD * 16;
 __global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestParams p) {
   extern __shared__ __align__(16) uint4 tiles[];   // [8 slots][128 rows x 8 chunks + pad]
-  uint32_t bid = blockIdx.x;
+  uint32_t jj = 0;
+  while (jj + 1 < p.njobs && blockIdx.x >= p.job[jj + 1].block_begin) ++jj;
+  const IngestJob &jb = p.job[jj];
+  uint32_t bid = blockIdx.x - jb.block_begin;
   const uint32_t g8 = bid % p.groups8;
   bid /= p.groups8;
-  const uint32_t kc = bid % p.kch;
-  const uint32_t mb = bid / p.kch;
+  const uint32_t kc = bid % jb.kch;
+  const uint32_t mb = bid / jb.kch;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = lane & 7, msub = lane >> 3;
   const uint64_t slot = (uint64_t)g8 * 8 + s;
@@ -177,8 +215,8 @@ __global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestP
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) {
       const uint32_t k = kc * KCHUNK + k_oct * 8 + kk;
-      v[kk] = (slot_ok && m < p.M && k < p.d0)
-                  ? __ldcs(p.ct + ((((uint64_t)c * p.d0 + k) * 2 + r) * p.L + l) * p.N + t)
+      v[kk] = (slot_ok && m < jb.M && k < jb.d0)
+                  ? __ldcs(jb.ct + ((((uint64_t)c * jb.d0 + k) * 2 + r) * p.L + l) * p.N + t)
                   : 0u;
     }
 #pragma unroll
@@ -197,7 +235,7 @@ __global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestP
     const int ss = idx >> 10;
     const uint64_t sl = (uint64_t)g8 * 8 + ss;
     if (sl >= (uint64_t)p.L * p.N) continue;
-    p.a_tiles[((sl * p.mblk + mb) * p.kch + kc) * 1024 + (idx & 1023)] = tiles[ss * TILE_PAD + (idx & 1023)];
+    jb.a_tiles[((sl * jb.mblk + mb) * jb.kch + kc) * 1024 + (idx & 1023)] = tiles[ss * TILE_PAD + (idx & 1023)];
   }
 }
 
@@ -278,7 +316,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const uint32_t kgroups = (p.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
 
   // A bounded wait that also gives up when another role already gave up.
   auto wait = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
@@ -303,13 +340,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       uint32_t st = 0, ph = 0;
       bool ok = true;
       for (uint64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
-        const uint32_t mb = (uint32_t)(u % p.mblk);
-        const uint64_t r = u / p.mblk;
-        const uint32_t nb = (uint32_t)(r % p.nblk);
-        const uint64_t slot = r / p.nblk;
-        const uint8_t *a_src = (const uint8_t *)p.a_tiles + ((slot * p.mblk + mb) * p.kch) * (uint64_t)A_TILE_BYTES;
-        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
-        for (uint32_t kc = 0; kc < p.kch; ++kc) {
+        const UnitRef ur = decode_unit(p, u);
+        const TcJob &jb = p.job[ur.j];
+        const uint8_t *a_src =
+            (const uint8_t *)jb.a_tiles + ((ur.slot * jb.mblk + ur.mb) * jb.kch) * (uint64_t)A_TILE_BYTES;
+        const uint8_t *b_src =
+            (const uint8_t *)jb.b_tiles + ((ur.slot * jb.nblk + ur.nb) * jb.kch) * (uint64_t)B_TILE_BYTES;
+        for (uint32_t kc = 0; kc < jb.kch; ++kc) {
           if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
           uint8_t *sa = smem + st * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
@@ -333,12 +370,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       uint32_t aph[2] = {0, 0};
       bool ok = true;
       for (uint64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        const uint32_t kch = p.job[decode_unit(p, u).j].kch;
+        const uint32_t kgroups = (kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
         for (uint32_t g = 0; g < kgroups && ok; ++g) {
           if (!(ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) break;
           tc_fence_after();
           const uint32_t tmem_d = tmem_base + buf * 256;
           const uint32_t c0 = g * KGROUP_CHUNKS;
-          const uint32_t c1 = min(p.kch, c0 + KGROUP_CHUNKS);
+          const uint32_t c1 = min(kch, c0 + KGROUP_CHUNKS);
           for (uint32_t kc = c0; kc < c1; ++kc) {
             if (!(ok = wait(&full[st], ph, kErrTmaWait))) break;
             tc_fence_after();
@@ -378,11 +417,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
     uint32_t aph[2] = {0, 0};
     bool ok = true;
     for (uint64_t un = blockIdx.x; un < p.units && ok; un += gridDim.x) {
-      const uint32_t mb = (uint32_t)(un % p.mblk);
-      const uint64_t r = un / p.mblk;
-      const uint32_t nb = (uint32_t)(r % p.nblk);
-      const uint64_t slot = r / p.nblk;
-      const uint32_t l = (uint32_t)(slot / p.N), t = (uint32_t)(slot % p.N);
+      const UnitRef ur = decode_unit(p, un);
+      const TcJob &jb = p.job[ur.j];
+      const uint32_t mb = ur.mb, nb = ur.nb;
+      const uint32_t kgroups = (jb.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
+      const uint32_t l = (uint32_t)(ur.slot / p.N), t = (uint32_t)(ur.slot % p.N);
       const TcLimb &lm = p.limb[l];
       const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
       // fp32 D + 1.5*2^23 has bit pattern 0x4B400000 + D for |D| <= 2^22, so
@@ -424,14 +463,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       }
       if (!ok) break;
       const uint32_t m = mb * MROWS + m_local;
-      if (m < p.M) {
+      if (m < jb.M) {
         const uint32_t c = m >> 1, rr = m & 1;
 #pragma unroll
         for (int j = 0; j < CHUNKS; ++j) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const uint32_t n = nb * NCOLS + (jbase + j) * 8 + h * 4 + u;
-            if (n < p.d1) p.out[((((uint64_t)c * p.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
+            if (n < jb.d1) jb.out[((((uint64_t)c * jb.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
           }
         }
       }
@@ -495,71 +534,188 @@ int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
 
+// ---- host side: shared launch helper ----------------------------------------
+
+namespace {
+
+struct TcShape {
+  uint32_t M, mblk, nblk, kch;
+  uint64_t slots;
+  size_t a_bytes;       // digit-tile workspace of this job
+};
+
+TcShape tc_shape(const gpir_db *db, uint32_t batch) {
+  TcShape sh;
+  sh.M = 2 * batch;
+  sh.mblk = (sh.M + MROWS - 1) / MROWS;
+  sh.nblk = (db->d1 + NCOLS - 1) / NCOLS;
+  sh.kch = (db->d0 + KCHUNK - 1) / KCHUNK;
+  sh.slots = (uint64_t)db->params.num_limbs * db->params.n;
+  sh.a_bytes = (size_t)sh.slots * sh.mblk * sh.kch * A_TILE_BYTES;
+  return sh;
+}
+
+std::mutex g_attr_mu;
+bool g_attr_done[64];
+
+int tc_set_attributes() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done[dev]) return GPIR_OK;
+  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INGEST_SMEM);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  g_attr_done[dev] = true;
+  return GPIR_OK;
+}
+
+// Ingest + persistent GEMM for up to MAX_JOBS problems sharing (N, L, primes);
+// job k's digit tiles go to ws + a_off[k]. Two launches on `stream`.
+int tc_launch_jobs(const gpir_job_t *jobs, uint32_t njobs, uint8_t *ws, const size_t *a_off, cudaStream_t stream) {
+  if (njobs == 0 || njobs > (uint32_t)MAX_JOBS) return GPIR_EINVAL;
+  int rc = tc_set_attributes();
+  if (rc != GPIR_OK) return rc;
+  const gpir_params &prm = jobs[0].db->params;
+  const uint32_t L = prm.num_limbs, N = prm.n;
+  const uint64_t slots = (uint64_t)L * N;
+
+  IngestParams ip;
+  memset(&ip, 0, sizeof(ip));
+  ip.L = L;
+  ip.N = N;
+  ip.groups8 = (uint32_t)((slots + 7) / 8);
+  ip.njobs = njobs;
+  TcParams tp;
+  memset(&tp, 0, sizeof(tp));
+  tp.L = L;
+  tp.N = N;
+  tp.njobs = njobs;
+  tp.err = device_error_word();
+  uint64_t blocks = 0, units = 0;
+  for (uint32_t k = 0; k < njobs; ++k) {
+    const gpir_db *db = jobs[k].db;
+    if (!db->db_digits) return GPIR_ENOTSUP;
+    const TcShape sh = tc_shape(db, jobs[k].batch);
+    IngestJob &ij = ip.job[k];
+    ij.ct = jobs[k].ct;
+    ij.a_tiles = reinterpret_cast<uint4 *>(ws + a_off[k]);
+    ij.M = sh.M;
+    ij.d0 = db->d0;
+    ij.mblk = sh.mblk;
+    ij.kch = sh.kch;
+    ij.block_begin = (uint32_t)blocks;
+    blocks += (uint64_t)ip.groups8 * sh.mblk * sh.kch;
+    TcJob &tj = tp.job[k];
+    tj.a_tiles = reinterpret_cast<const uint16_t *>(ws + a_off[k]);
+    tj.b_tiles = db->db_digits;
+    tj.out = jobs[k].out;
+    tj.M = sh.M;
+    tj.d0 = db->d0;
+    tj.d1 = db->d1;
+    tj.mblk = sh.mblk;
+    tj.nblk = sh.nblk;
+    tj.kch = sh.kch;
+    tj.unit_begin = units;
+    units += slots * sh.mblk * sh.nblk;
+    if (blocks > 0x7fffffffull) return GPIR_EINVAL;
+  }
+  tp.units = units;
+  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(prm.primes[l]);
+  tc_ingest_kernel<<<(unsigned)blocks, INGEST_THREADS, INGEST_SMEM, stream>>>(ip);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int grid = (int)std::min<uint64_t>((uint64_t)sm_count(), units);
+  tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, stream>>>(tp);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+// Workspace shared by multi-job launches on each device (grown on demand,
+// never while the stream is being captured).
+std::mutex g_multi_mu;
+void *g_multi_ws[64];
+size_t g_multi_ws_bytes[64];
+
+}  // namespace
+
 int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
                      cudaStream_t stream) {
   (void)variant;
   gpir_db *db = const_cast<gpir_db *>(db_c);
   if (!db->db_digits) return GPIR_ENOTSUP;
-  const uint32_t L = db->params.num_limbs, N = db->params.n, M = 2 * batch;
-  const uint32_t mblk = (M + MROWS - 1) / MROWS, nblk = (db->d1 + NCOLS - 1) / NCOLS;
-  const uint32_t kch = (db->d0 + KCHUNK - 1) / KCHUNK;
-  const uint64_t slots = (uint64_t)L * N;
-  const size_t a_bytes = (size_t)slots * mblk * kch * A_TILE_BYTES;
-  if (db->tc_ws_bytes < a_bytes) {
+  const TcShape sh = tc_shape(db, batch);
+  if (db->tc_ws_bytes < sh.a_bytes) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(stream, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return GPIR_ENOMEM;   // cannot allocate inside a capture
     if (db->tc_ws) {
       cudaStreamSynchronize(stream);
       cudaFree(db->tc_ws);
     }
     db->tc_ws = nullptr;
     db->tc_ws_bytes = 0;
-    cudaError_t e = cudaMalloc(&db->tc_ws, a_bytes);
+    cudaError_t e = cudaMalloc(&db->tc_ws, sh.a_bytes);
     if (e != cudaSuccess) return set_cuda_error(e);
-    db->tc_ws_bytes = a_bytes;
+    db->tc_ws_bytes = sh.a_bytes;
   }
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INGEST_SMEM);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    attr_done = true;
-  }
-  IngestParams ip;
-  ip.M = M;
-  ip.d0 = db->d0;
-  ip.L = L;
-  ip.N = N;
-  ip.mblk = mblk;
-  ip.kch = kch;
-  ip.groups8 = (uint32_t)((slots + 7) / 8);
-  ip.ct = ct;
-  ip.a_tiles = reinterpret_cast<uint4 *>(db->tc_ws);
-  const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
-  if (igrid > 0x7fffffffull) return GPIR_EINVAL;
-  tc_ingest_kernel<<<(unsigned)igrid, INGEST_THREADS, INGEST_SMEM, stream>>>(ip);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return set_cuda_error(e);
+  gpir_job_t job;
+  job.db = db;
+  job.batch = batch;
+  job.reserved = 0;
+  job.ct = ct;
+  job.out = out;
+  const size_t off = 0;
+  return tc_launch_jobs(&job, 1, reinterpret_cast<uint8_t *>(db->tc_ws), &off, stream);
+}
 
-  TcParams tp;
-  memset(&tp, 0, sizeof(tp));
-  tp.M = M;
-  tp.d0 = db->d0;
-  tp.d1 = db->d1;
-  tp.L = L;
-  tp.N = N;
-  tp.mblk = mblk;
-  tp.nblk = nblk;
-  tp.kch = kch;
-  tp.units = slots * mblk * nblk;
-  tp.a_tiles = reinterpret_cast<const uint16_t *>(db->tc_ws);
-  tp.b_tiles = db->db_digits;
-  tp.out = out;
-  tp.err = device_error_word();
-  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(db->params.primes[l]);
-  const int grid = (int)std::min<uint64_t>((uint64_t)sm_count(), tp.units);
-  tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, stream>>>(tp);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {
+  size_t total = 0;
+  for (uint32_t k = 0; k < njobs; ++k) total += (tc_shape(jobs[k].db, jobs[k].batch).a_bytes + 1023) & ~(size_t)1023;
+  return total;
+}
+
+int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  const size_t need = rowsel_tc_multi_workspace(jobs, njobs);
+  uint8_t *ws;
+  {
+    std::lock_guard<std::mutex> lk(g_multi_mu);
+    if (g_multi_ws_bytes[dev] < need) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(stream, &cs);
+      if (cs != cudaStreamCaptureStatusNone) return GPIR_ENOMEM;
+      if (g_multi_ws[dev]) {
+        cudaDeviceSynchronize();
+        cudaFree(g_multi_ws[dev]);
+      }
+      g_multi_ws[dev] = nullptr;
+      g_multi_ws_bytes[dev] = 0;
+      e = cudaMalloc(&g_multi_ws[dev], need);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      g_multi_ws_bytes[dev] = need;
+    }
+    ws = reinterpret_cast<uint8_t *>(g_multi_ws[dev]);
+  }
+  // MAX_JOBS problems per launch; their workspaces do not overlap.
+  size_t off[MAX_JOBS];
+  size_t base = 0;
+  for (uint32_t k0 = 0; k0 < njobs; k0 += MAX_JOBS) {
+    const uint32_t n = std::min<uint32_t>(MAX_JOBS, njobs - k0);
+    for (uint32_t k = 0; k < n; ++k) {
+      off[k] = base;
+      base += (tc_shape(jobs[k0 + k].db, jobs[k0 + k].batch).a_bytes + 1023) & ~(size_t)1023;
+    }
+    int rc = tc_launch_jobs(jobs + k0, n, ws, off, stream);
+    if (rc != GPIR_OK) return rc;
+  }
+  return GPIR_OK;
 }
 
 }  // namespace gpir
@@ -597,10 +753,8 @@ int noalloc_setup(int dev, void **tiles) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tiles);
     if (e != cudaSuccess) return set_cuda_error(e);
-    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_ingest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INGEST_SMEM);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    int rc = tc_set_attributes();
+    if (rc != GPIR_OK) return rc;
     g_noalloc_addr[dev] = p;
   }
   *tiles = g_noalloc_addr[dev];
@@ -621,7 +775,7 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
   const size_t out_bytes = (size_t)batch * db->d1 * 2 * slots * 4;
   const uintptr_t a0 = (uintptr_t)ct_dev, a1 = a0 + ct_bytes, b0 = (uintptr_t)out_dev, b1 = b0 + out_bytes;
   if (a0 < b1 && b0 < a1) return GPIR_EINVAL;
-  const uint32_t mblk = (M + MROWS - 1) / MROWS, nblk = (db->d1 + NCOLS - 1) / NCOLS;
+  const uint32_t mblk = (M + MROWS - 1) / MROWS;
   const uint32_t kch = (db->d0 + KCHUNK - 1) / KCHUNK;
   const uint64_t a_bytes = slots * mblk * kch * (uint64_t)A_TILE_BYTES;
   if (a_bytes > (uint64_t)GPIR_NOALLOC_SCRATCH_BYTES) return GPIR_ETOOBIG;
@@ -632,45 +786,12 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
   void *tiles = nullptr;
   int rc = noalloc_setup(dev, &tiles);
   if (rc != GPIR_OK) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-
-  IngestParams ip;
-  ip.M = M;
-  ip.d0 = db->d0;
-  ip.L = L;
-  ip.N = N;
-  ip.mblk = mblk;
-  ip.kch = kch;
-  ip.groups8 = (uint32_t)((slots + 7) / 8);
-  ip.ct = ct_dev;
-  ip.a_tiles = reinterpret_cast<uint4 *>(tiles);
-  const uint64_t igrid = (uint64_t)ip.groups8 * mblk * kch;
-  if (igrid > 0x7fffffffull) return GPIR_EINVAL;
-  tc_ingest_kernel<<<(unsigned)igrid, INGEST_THREADS, INGEST_SMEM, s>>>(ip);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return set_cuda_error(e);
-
-  TcParams tp;
-  memset(&tp, 0, sizeof(tp));
-  tp.M = M;
-  tp.d0 = db->d0;
-  tp.d1 = db->d1;
-  tp.L = L;
-  tp.N = N;
-  tp.mblk = mblk;
-  tp.nblk = nblk;
-  tp.kch = kch;
-  tp.units = slots * mblk * nblk;
-  tp.a_tiles = reinterpret_cast<const uint16_t *>(tiles);
-  tp.b_tiles = db->db_digits;
-  tp.out = out_dev;
-  tp.err = device_error_word();
-  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(db->params.primes[l]);
-  int sms = 0;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return set_cuda_error(e);
-  const int grid = (int)std::min<uint64_t>((uint64_t)sms, tp.units);
-  tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(tp);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+  gpir_job_t job;
+  job.db = db;
+  job.batch = batch;
+  job.reserved = 0;
+  job.ct = ct_dev;
+  job.out = out_dev;
+  const size_t off = 0;
+  return tc_launch_jobs(&job, 1, reinterpret_cast<uint8_t *>(tiles), &off, (cudaStream_t)stream);
 }

@@ -61,6 +61,9 @@ def _load():
         "gpir_rowsel_batch_host": (I, [P, U32, P, P, I, P]),
         "gpir_rowsel_multi": (I, [ctypes.POINTER(gpir_job_t), U32, I, P]),
         "gpir_rowsel_batch_noalloc": (I, [P, U32, P, P, P]),
+        "gpir_graph_create": (I, [ctypes.POINTER(gpir_job_t), U32, I, P, ctypes.POINTER(P)]),
+        "gpir_graph_launch": (I, [P, P]),
+        "gpir_graph_destroy": (I, [P]),
         "gpir_sync": (I, [P, U32]),
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
@@ -159,13 +162,33 @@ def gpir_rowsel_batch_noalloc(db, batch, ct_dev, out_dev, stream=None):
 
 def gpir_rowsel_multi(jobs, path=GPIR_PATH_AUTO, stream=None):
     """jobs: sequence of (db_handle, batch, ct_dev, out_dev)."""
+    return _check(lib.gpir_rowsel_multi(_jobs(jobs), len(jobs), int(path), _stream(stream)), "gpir_rowsel_multi")
+
+
+def _jobs(jobs):
     arr = (gpir_job_t * len(jobs))()
     for k, (db, batch, ct, out) in enumerate(jobs):
         arr[k].db = db.value if isinstance(db, ctypes.c_void_p) else db
         arr[k].batch = int(batch)
         arr[k].ct = _ptr(ct)
         arr[k].out = _ptr(out)
-    return _check(lib.gpir_rowsel_multi(arr, len(jobs), int(path), _stream(stream)), "gpir_rowsel_multi")
+    return arr
+
+
+def gpir_graph_create(jobs, path=GPIR_PATH_AUTO, stream=None):
+    """Capture one gpir_rowsel_multi call over `jobs` into a CUDA graph."""
+    h = ctypes.c_void_p()
+    _check(lib.gpir_graph_create(_jobs(jobs), len(jobs), int(path), _stream(stream), ctypes.byref(h)),
+           "gpir_graph_create")
+    return h
+
+
+def gpir_graph_launch(graph, stream=None):
+    return _check(lib.gpir_graph_launch(graph, _stream(stream)), "gpir_graph_launch")
+
+
+def gpir_graph_destroy(graph):
+    return lib.gpir_graph_destroy(graph)
 
 
 def gpir_sync(stream=None, timeout_ms=0):
