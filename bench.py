@@ -314,6 +314,51 @@ class GpuWorkload:
         self.g.gpir_params_destroy(self.params)
 
 
+def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
+    """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
+    512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
+    one-hot selection drawn from a per-DB pool; p50/p99 latency and queries/s."""
+    from paper_2604_04696_gb300.server import Request, ResidentDb, Server, poisson_arrivals, toy_rlwe_query
+    c = synth.config_shapes("c5_serving")
+    N, L, primes = c["N"], c["L"], list(c["primes"])
+    params = g.gpir_params_create(N, primes)
+    dbs, pools = [], []
+    rng = np.random.default_rng(seed)
+    for k, (D0, D1) in enumerate(c["dbs"]):
+        db = torch.empty(D0 * D1 * L * N, dtype=torch.int32, device="cuda")
+        g.gpir_fill_uniform(db, db.numel(), 0, seed * 10 + k, synth.TAG_DB, params, N)
+        h = g.gpir_db_upload(params, D0, D1, db, True, 0)
+        del db
+        dbs.append(ResidentDb(h, D0, D1, N, L))
+        pool = []
+        for qi in range(4):
+            ct, _ = toy_rlwe_query(params, D0, L, N, primes, int(rng.integers(0, D0)), seed * 100 + k * 10 + qi)
+            pool.append(ct.cpu().pin_memory())
+            del ct
+        pools.append(pool)
+    torch.cuda.synchronize()
+    srv = Server(dbs, mem_budget_bytes=16 << 30, max_batch=32, n_streams=3)
+    # warm-up: one short burst (autotune-free path; sizes the per-stream workspaces)
+    warm = [Request(i, i % 3, pools[i % 3][0], 0.0) for i in range(3 * 32 * 3)]
+    srv.run(warm)
+    out = []
+    for rate in rates:
+        n = max(50, int(rate * seconds))
+        arr = poisson_arrivals(float(rate), n, seed=seed + rate)
+        reqs = []
+        for i, t in enumerate(arr):
+            d = int(rng.integers(0, 3))
+            reqs.append(Request(i, d, pools[d][int(rng.integers(0, 4))], float(t)))
+        st = srv.run(reqs)
+        out.append({"offered_qps": rate, "queries_s": st["queries_s"], "p50_ms": st["p50_ms"],
+                    "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "requests": st["requests"],
+                    "rejected": st["rejected"]})
+    for d in dbs:
+        g.gpir_db_free(d.h)
+    g.gpir_params_destroy(params)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,6 +456,9 @@ def main():
                               "roofline_frac": roofline(path, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
+        line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "
+                                       "Poisson arrivals, toy-RLWE one-hot queries, 3 streams, max batch 32",
+                           "rates": run_serving(g, torch)}
         if world == 1:
             v, n, dt = oracle_queries_per_s(w, seconds_target=10.0)
             line["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",

@@ -107,7 +107,10 @@ size_t gpir_db_device_bytes(const gpir_db_t *db);
  * must not overlap. Inputs must be canonical residues (< q_l): this is a
  * precondition, not checked, because a check would add a pass over the
  * ciphertext stream. Results are canonical and identical for every path.
- * GPIR_ENOTSUP if `path` was not prepared at upload. Asynchronous. */
+ * GPIR_ENOTSUP if `path` was not prepared at upload. The tensor-core path
+ * keeps its per-batch digit tiles (2x the ciphertext bytes) in a workspace
+ * owned by the library per (device, stream), grown on demand; calls on
+ * different streams may overlap. Asynchronous. */
 int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                       uint32_t *out_dev, int path, void *stream);
 
@@ -129,7 +132,8 @@ int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *
  * it. All jobs must share the same params (N, L, primes) and every job's
  * ct / out must not overlap any other buffer of the call. The tensor-core
  * workspace for the call is grown on demand (not while the stream is being
- * captured: GPIR_ENOMEM then). Asynchronous. */
+ * captured: GPIR_ENOMEM then); it is per (device, stream), so calls on
+ * different streams may run concurrently. Asynchronous. */
 int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream);
 
 /* CUDA-graph plan of one gpir_rowsel_multi call (the paper replays its
@@ -137,7 +141,9 @@ int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *st
  * once eagerly on `stream` (sizing workspaces; synchronizes), then captures
  * it; launch replays it on any stream. The job list (buffers, batch sizes)
  * is fixed at creation: refill the same ct buffers and replay. `stream` must
- * not be the legacy default stream. */
+ * not be the legacy default stream. The graph's tensor-core workspace is the
+ * one of the creating stream: do not replay it concurrently with other work
+ * issued to that stream, or with another replay of the same graph. */
 typedef struct gpir_graph gpir_graph_t;
 int gpir_graph_create(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream,
                       gpir_graph_t **out);

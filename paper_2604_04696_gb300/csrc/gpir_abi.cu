@@ -304,7 +304,6 @@ int gpir_db_free(gpir_db_t *db) {
   if (db->db_digits) cudaFree(db->db_digits);
   if (db->ws_ct) cudaFree(db->ws_ct);
   if (db->ws_out) cudaFree(db->ws_out);
-  if (db->tc_ws) cudaFree(db->tc_ws);
   delete db->variants;
   delete db->mu;
   delete db;

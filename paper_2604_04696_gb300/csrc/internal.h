@@ -49,9 +49,6 @@ struct gpir_db {
   // tcgen05 path: signed 8-bit digits as bf16, slot-major (see rowsel_tc.cu).
   uint16_t *db_digits;
   size_t db_digits_bytes;
-  // tcgen05 path: per-batch A-operand digit tiles (grown on demand).
-  void *tc_ws;
-  size_t tc_ws_bytes;
   // Host-buffer entry point workspace.
   uint32_t *ws_ct, *ws_out;
   size_t ws_ct_bytes, ws_out_bytes;

@@ -41,6 +41,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -634,42 +635,53 @@ int tc_launch_jobs(const gpir_job_t *jobs, uint32_t njobs, uint8_t *ws, const si
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
 
-// Workspace shared by multi-job launches on each device (grown on demand,
-// never while the stream is being captured).
-std::mutex g_multi_mu;
-void *g_multi_ws[64];
-size_t g_multi_ws_bytes[64];
+// Digit-tile workspaces, one per (device, stream): work on one stream runs in
+// order, so a stream's workspace is never used by two launches at once.
+// Grown on demand (after draining that stream), never while the stream is
+// being captured.
+struct Workspace {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  Workspace &w = g_ws[{dev, stream}];
+  if (w.bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(stream, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return GPIR_ENOMEM;   // no allocation inside a capture
+    if (w.ptr) {
+      cudaStreamSynchronize(stream);
+      cudaFree(w.ptr);
+    }
+    w.ptr = nullptr;
+    w.bytes = 0;
+    e = cudaMalloc(&w.ptr, need);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    w.bytes = need;
+  }
+  *out = reinterpret_cast<uint8_t *>(w.ptr);
+  return GPIR_OK;
+}
 
 }  // namespace
 
-int rowsel_tc_launch(const gpir_db *db_c, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
+int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
                      cudaStream_t stream) {
   (void)variant;
-  gpir_db *db = const_cast<gpir_db *>(db_c);
-  if (!db->db_digits) return GPIR_ENOTSUP;
-  const TcShape sh = tc_shape(db, batch);
-  if (db->tc_ws_bytes < sh.a_bytes) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(stream, &cs);
-    if (cs != cudaStreamCaptureStatusNone) return GPIR_ENOMEM;   // cannot allocate inside a capture
-    if (db->tc_ws) {
-      cudaStreamSynchronize(stream);
-      cudaFree(db->tc_ws);
-    }
-    db->tc_ws = nullptr;
-    db->tc_ws_bytes = 0;
-    cudaError_t e = cudaMalloc(&db->tc_ws, sh.a_bytes);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    db->tc_ws_bytes = sh.a_bytes;
-  }
   gpir_job_t job;
   job.db = db;
   job.batch = batch;
   job.reserved = 0;
   job.ct = ct;
   job.out = out;
-  const size_t off = 0;
-  return tc_launch_jobs(&job, 1, reinterpret_cast<uint8_t *>(db->tc_ws), &off, stream);
+  return rowsel_tc_multi(&job, 1, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {
@@ -679,30 +691,11 @@ size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {
 }
 
 int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_cuda_error(e);
-  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
-  const size_t need = rowsel_tc_multi_workspace(jobs, njobs);
-  uint8_t *ws;
-  {
-    std::lock_guard<std::mutex> lk(g_multi_mu);
-    if (g_multi_ws_bytes[dev] < need) {
-      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-      cudaStreamIsCapturing(stream, &cs);
-      if (cs != cudaStreamCaptureStatusNone) return GPIR_ENOMEM;
-      if (g_multi_ws[dev]) {
-        cudaDeviceSynchronize();
-        cudaFree(g_multi_ws[dev]);
-      }
-      g_multi_ws[dev] = nullptr;
-      g_multi_ws_bytes[dev] = 0;
-      e = cudaMalloc(&g_multi_ws[dev], need);
-      if (e != cudaSuccess) return set_cuda_error(e);
-      g_multi_ws_bytes[dev] = need;
-    }
-    ws = reinterpret_cast<uint8_t *>(g_multi_ws[dev]);
-  }
+  for (uint32_t k = 0; k < njobs; ++k)
+    if (!jobs[k].db->db_digits) return GPIR_ENOTSUP;
+  uint8_t *ws = nullptr;
+  int rc0 = stream_workspace(stream, rowsel_tc_multi_workspace(jobs, njobs), &ws);
+  if (rc0 != GPIR_OK) return rc0;
   // MAX_JOBS problems per launch; their workspaces do not overlap.
   size_t off[MAX_JOBS];
   size_t base = 0;
