@@ -67,6 +67,7 @@ struct TcLimb {
   uint32_t pad;
   uint64_t mu;        // floor(2^64 / q)
   uint64_t off;       // multiple of q, >= 2^55: makes signed sums non-negative
+  int64_t kfix;       // 0x4B400000 * sum_{u,v} c[u+v] (see the epilogue)
   int32_t c[8];       // 2^(8s) mod q, s = 0..6 (c[7] unused)
 };
 
@@ -174,26 +175,35 @@ __device__ __forceinline__ uint32_t digit_bf16_bits(uint32_t x, int u) {
 // ---- ingest: p-major ciphertexts -> A-operand digit tiles --------------------
 
 struct IngestJob {
-  const uint32_t *ct;
   uint4 *a_tiles;
   uint32_t M, d0, mblk, kch;
   uint32_t block_begin;                 // first CTA of this job
 };
 
 struct IngestParams {
-  uint32_t L, N, groups8, njobs;
+  uint32_t L, N, gpl, groups8, njobs;   // gpl: 8-slot groups per limb
+  unsigned int *err;
   IngestJob job[MAX_JOBS];
+  CUtensorMap ct_map[MAX_JOBS];         // p-major ct [B][D0][2][L][N], box (8 slots, 1, 2, 64 k, 16 clients)
 };
 
-// One CTA: 8 consecutive slots x one m-block (32 rows) x one k-chunk (64 k).
-// Each slot's 16 KB tile is staged in shared memory with a 16-byte pad after
-// it, so the 8 lanes of a store phase (8 different slots) hit 8 different
-// bank groups.
+// One CTA: 8 consecutive slots of one limb x one m-block (32 rows = 16
+// clients x 2 polynomials) x one k-chunk (64 k). One TMA box brings the raw
+// residues ([16 clients][64 k][2][8 slots], 64 KB, zero-filled outside the
+// tensor) into shared memory; threads split them into digits and build the 8
+// slots' A tiles in shared memory, each followed by a 16-byte pad so the 8
+// lanes of a store phase (8 different slots) hit 8 different bank groups;
+// the tiles then leave with coalesced 16-byte stores.
 constexpr int INGEST_THREADS = 512;
 constexpr int TILE_PAD = 1025;                       // uint4 per staged tile incl. pad
-constexpr size_t INGEST_SMEM = 8 * TILE_PAD * 16;
-__global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestParams p) {
-  extern __shared__ __align__(16) uint4 tiles[];   // [8 slots][128 rows x 8 chunks + pad]
+constexpr int RAW_BYTES = 16 * KCHUNK * 2 * 8 * 4;   // 64 KB raw box
+constexpr size_t INGEST_SMEM = 1024 + RAW_BYTES + 8 * TILE_PAD * 16 + 64;
+__global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const __grid_constant__ IngestParams p) {
+  extern __shared__ __align__(1024) uint8_t ing_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)ing_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t *raw = reinterpret_cast<const uint32_t *>(base);
+  uint4 *tiles = reinterpret_cast<uint4 *>(base + RAW_BYTES);    // [8 slots][128 rows x 8 chunks + pad]
+  uint64_t *bar = reinterpret_cast<uint64_t *>(base + RAW_BYTES + 8 * TILE_PAD * 16);
   uint32_t jj = 0;
   while (jj + 1 < p.njobs && blockIdx.x >= p.job[jj + 1].block_begin) ++jj;
   const IngestJob &jb = p.job[jj];
@@ -202,40 +212,52 @@ __global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const IngestP
   bid /= p.groups8;
   const uint32_t kc = bid % jb.kch;
   const uint32_t mb = bid / jb.kch;
+  const uint32_t l = g8 / p.gpl, t0 = (g8 % p.gpl) * 8;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, RAW_BYTES);
+    tma_load_5d(base, &p.ct_map[jj], bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK), (int)(mb * (MROWS / 2)));
+  }
+  const bool ok = mbar_wait_bounded(bar, 0, p.err, kErrTmaWait);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = lane & 7, msub = lane >> 3;
-  const uint64_t slot = (uint64_t)g8 * 8 + s;
-  const bool slot_ok = slot < (uint64_t)p.L * p.N;
-  const uint32_t l = slot_ok ? (uint32_t)(slot / p.N) : 0, t = slot_ok ? (uint32_t)(slot % p.N) : 0;
-  for (int task = warp; task < 64; task += INGEST_THREADS / 32) {
-    const int m_local = (task >> 3) * 4 + msub;
-    const int k_oct = task & 7;
-    const uint32_t m = mb * MROWS + m_local;
-    const uint32_t c = m >> 1, r = m & 1;
-    uint32_t v[8];
+  if (ok) {
+    // Each warp owns 64 / 16 = 4 (m-quad, k-octet) tasks.
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-      const uint32_t k = kc * KCHUNK + k_oct * 8 + kk;
-      v[kk] = (slot_ok && m < jb.M && k < jb.d0)
-                  ? __ldcs(jb.ct + ((((uint64_t)c * jb.d0 + k) * 2 + r) * p.L + l) * p.N + t)
-                  : 0u;
-    }
+    for (int tt = 0; tt < 64 / (INGEST_THREADS / 32); ++tt) {
+      const int task = warp + tt * (INGEST_THREADS / 32);
+      const int m_local = (task >> 3) * 4 + msub;
+      const int k_oct = task & 7;
+      const int c = m_local >> 1, r = m_local & 1;
+      uint32_t v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      uint4 w;
-      w.x = digit_bf16_bits(v[0], u) | (digit_bf16_bits(v[1], u) << 16);
-      w.y = digit_bf16_bits(v[2], u) | (digit_bf16_bits(v[3], u) << 16);
-      w.z = digit_bf16_bits(v[4], u) | (digit_bf16_bits(v[5], u) << 16);
-      w.w = digit_bf16_bits(v[6], u) | (digit_bf16_bits(v[7], u) << 16);
-      const int row = (m_local >> 3) * 32 + u * 8 + (m_local & 7);
-      tiles[s * TILE_PAD + row * 8 + (k_oct ^ (row & 7))] = w;
+      for (int kk = 0; kk < 8; ++kk) v[kk] = raw[((c * KCHUNK + k_oct * 8 + kk) * 2 + r) * 8 + s];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint4 w;
+        w.x = digit_bf16_bits(v[0], u) | (digit_bf16_bits(v[1], u) << 16);
+        w.y = digit_bf16_bits(v[2], u) | (digit_bf16_bits(v[3], u) << 16);
+        w.z = digit_bf16_bits(v[4], u) | (digit_bf16_bits(v[5], u) << 16);
+        w.w = digit_bf16_bits(v[6], u) | (digit_bf16_bits(v[7], u) << 16);
+        const int row = (m_local >> 3) * 32 + u * 8 + (m_local & 7);
+        tiles[s * TILE_PAD + row * 8 + (k_oct ^ (row & 7))] = w;
+      }
     }
   }
   __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) mbar_wait_bounded(bar, 0, nullptr, 0);   // let a late copy land first
+    return;
+  }
   for (int idx = threadIdx.x; idx < 8 * 1024; idx += INGEST_THREADS) {
     const int ss = idx >> 10;
-    const uint64_t sl = (uint64_t)g8 * 8 + ss;
-    if (sl >= (uint64_t)p.L * p.N) continue;
+    const uint32_t t = t0 + ss;
+    if (t >= p.N) continue;
+    const uint64_t sl = (uint64_t)l * p.N + t;
     jb.a_tiles[((sl * jb.mblk + mb) * jb.kch + kc) * 1024 + (idx & 1023)] = tiles[ss * TILE_PAD + (idx & 1023)];
   }
 }
@@ -426,8 +448,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
       const TcLimb &lm = p.limb[l];
       const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
       // fp32 D + 1.5*2^23 has bit pattern 0x4B400000 + D for |D| <= 2^22, so
-      // sum_v bits_v * c_v - 0x4B400000 * sum_v c_v = sum_v D_v * c_v exactly.
-      const int64_t kfix = (int64_t)0x4B400000 * ((int64_t)c0 + c1 + c2 + c3);
+      // sum_{u,v} bits_uv c_{u+v} - lm.kfix = sum_{u,v} D_uv c_{u+v} exactly
+      // (|bits * c| < 2^58.3: the 16-term sum stays below 2^63).
+      const bool odd = (u & 1) != 0, high = (u & 2) != 0;
       uint32_t res[2 * CHUNKS];
 #pragma unroll
       for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
@@ -440,20 +463,30 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
           uint32_t d[32];
           tmem_ld32(taddr + j * 32, d);
 #pragma unroll
-          for (int n8 = 0; n8 < 8; ++n8) {
-            const int32_t b0 = __float_as_int(__uint_as_float(d[n8 * 4 + 0]) + 12582912.0f);
-            const int32_t b1 = __float_as_int(__uint_as_float(d[n8 * 4 + 1]) + 12582912.0f);
-            const int32_t b2 = __float_as_int(__uint_as_float(d[n8 * 4 + 2]) + 12582912.0f);
-            const int32_t b3 = __float_as_int(__uint_as_float(d[n8 * 4 + 3]) + 12582912.0f);
-            int64_t sv = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3 - kfix;
-            sv += __shfl_xor_sync(0xffffffffu, sv, 8);
-            sv += __shfl_xor_sync(0xffffffffu, sv, 16);
-            if ((n8 & 3) == u) {
-              const uint32_t rr = reduce64((uint64_t)(sv + (int64_t)lm.off), lm.q, lm.mu);
-              uint32_t &acc = res[j * 2 + (n8 >> 2)];
-              acc += rr;
-              acc = acc >= lm.q ? acc - lm.q : acc;
+          for (int h = 0; h < 2; ++h) {
+            int64_t P[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const int n8 = h * 4 + w;
+              const int32_t b0 = __float_as_int(__uint_as_float(d[n8 * 4 + 0]) + 12582912.0f);
+              const int32_t b1 = __float_as_int(__uint_as_float(d[n8 * 4 + 1]) + 12582912.0f);
+              const int32_t b2 = __float_as_int(__uint_as_float(d[n8 * 4 + 2]) + 12582912.0f);
+              const int32_t b3 = __float_as_int(__uint_as_float(d[n8 * 4 + 3]) + 12582912.0f);
+              P[w] = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3;
             }
+            // Reduce-scatter over the 4 digit lanes u (lane bits 3-4): lane u
+            // ends with the sum over u' of P_u'[w = u], i.e. output n8 = 4h + u.
+            int64_t k0 = odd ? P[1] : P[0], k1 = odd ? P[3] : P[2];
+            const int64_t s0 = odd ? P[0] : P[1], s1 = odd ? P[2] : P[3];
+            k0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+            k1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+            int64_t keep = high ? k1 : k0;
+            const int64_t send = high ? k0 : k1;
+            keep += __shfl_xor_sync(0xffffffffu, send, 16);
+            const uint32_t rr = reduce64((uint64_t)(keep - lm.kfix + (int64_t)lm.off), lm.q, lm.mu);
+            uint32_t &acc = res[j * 2 + h];
+            acc += rr;
+            acc = acc >= lm.q ? acc - lm.q : acc;
           }
         }
         tc_fence_before();
@@ -499,6 +532,10 @@ static TcLimb make_limb(uint32_t q) {
     pw = (pw << 8) % q;
   }
   t.c[7] = 0;
+  int64_t csum = 0;
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) csum += t.c[u + v];
+  t.kfix = (int64_t)0x4B400000 * csum;
   return t;
 }
 
@@ -588,8 +625,10 @@ int tc_launch_jobs(const gpir_job_t *jobs, uint32_t njobs, uint8_t *ws, const si
   memset(&ip, 0, sizeof(ip));
   ip.L = L;
   ip.N = N;
-  ip.groups8 = (uint32_t)((slots + 7) / 8);
+  ip.gpl = (N + 7) / 8;
+  ip.groups8 = ip.gpl * L;
   ip.njobs = njobs;
+  ip.err = device_error_word();
   TcParams tp;
   memset(&tp, 0, sizeof(tp));
   tp.L = L;
@@ -602,7 +641,14 @@ int tc_launch_jobs(const gpir_job_t *jobs, uint32_t njobs, uint8_t *ws, const si
     if (!db->db_digits) return GPIR_ENOTSUP;
     const TcShape sh = tc_shape(db, jobs[k].batch);
     IngestJob &ij = ip.job[k];
-    ij.ct = jobs[k].ct;
+    {
+      const uint64_t dims[5] = {N, L, 2, db->d0, jobs[k].batch};
+      const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
+                               (uint64_t)db->d0 * 2 * L * N * 4};
+      const uint32_t box[5] = {8, 1, 2, (uint32_t)KCHUNK, (uint32_t)(MROWS / 2)};
+      int rc2 = encode_tiled_u32(&ip.ct_map[k], jobs[k].ct, 5, dims, str, box);
+      if (rc2 != GPIR_OK) return rc2;
+    }
     ij.a_tiles = reinterpret_cast<uint4 *>(ws + a_off[k]);
     ij.M = sh.M;
     ij.d0 = db->d0;
