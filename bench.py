@@ -181,7 +181,7 @@ def kernel_src_hash(path_id):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def recorded_traffic(path_id, workload, batch):
+def recorded_traffic(kernel, workload, batch, path_id):
     """DRAM bytes per launch from a committed ncu capture, or None when absent or
     when the kernel source changed since it was taken."""
     try:
@@ -189,10 +189,30 @@ def recorded_traffic(path_id, workload, batch):
             t = json.load(fh)
     except Exception:
         return None
-    e = t.get("%s/%s/B%d" % (PATH_NAMES[path_id], workload, batch))
+    e = t.get("%s/%s/B%d" % (kernel, workload, batch))
     if not e or e.get("src_sha") != kernel_src_hash(path_id):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def kernel_roofline(name, w, ms, peaks, workload):
+    """Roofline of one kernel: its algorithmic work per launch over its own
+    average launch time (CUDA events on its launch stream)."""
+    alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
+    s = ms / 1e3
+    path_id = {"rowsel_cc": 1, "rowsel_imma": 2, "tc_gemm": 4, "tc_ingest": 4}[name]
+    traffic = recorded_traffic(name, workload, w["B"], path_id)
+    if name == "tc_ingest":
+        b = sizes.query_ct_bytes(w["B"], w["D0"], w["N"], w["L"])
+        a = b / s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": a / peaks["hbm_gbs"], "traffic": traffic,
+                "note": "selection-ciphertext bytes (read once) per launch vs %s copy BW" % peaks["source"]}
+    r = roofline(path_id, w, ms, peaks, workload)
+    r["kernel"] = name
+    r["traffic"] = traffic
+    return r
 
 
 def roofline(path_id, w, ms, peaks, workload):
@@ -200,7 +220,7 @@ def roofline(path_id, w, ms, peaks, workload):
     macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     s = ms / 1e3
     t_hbm = alg / (peaks["hbm_gbs"] * 1e9)
-    traffic = recorded_traffic(path_id, workload, w["B"])
+    traffic = None
     if path_id == 4:
         flops = 2.0 * 16 * macs       # 16 exact bf16 digit products per modular MAC
         t_c = flops / (peaks["bf16_tflops"] * 1e12)
@@ -309,6 +329,20 @@ class GpuWorkload:
         ms = e0.elapsed_time(e1) / steps
         return ms, ct_h.numel() * 4, out_h.numel() * 4
 
+    def kernel_times(self, path, steps):
+        """Average device time per kernel of one step, from the library's
+        CUDA-event trace on the launch stream."""
+        g = self.g
+        g.gpir_trace_enable(True)
+        for _ in range(steps):
+            self.step(path)
+        recs = g.gpir_trace_read()
+        g.gpir_trace_enable(False)
+        tot = {}
+        for name, ms in recs:
+            tot.setdefault(name, []).append(ms)
+        return {k: sum(v) / len(v) for k, v in tot.items()}, {k: len(v) // steps for k, v in tot.items()}
+
     def close(self):
         self.g.gpir_db_free(self.h)
         self.g.gpir_params_destroy(self.params)
@@ -369,7 +403,13 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--path", default="auto", choices=list(PATH_IDS))
     ap.add_argument("--no-extras", action="store_true", help="skip path comparison, sweep and cpu baseline")
+    ap.add_argument("--peaks", action="store_true", help="build and run the peak-rate probe, then exit")
     args = ap.parse_args()
+    if args.peaks:
+        src = os.path.join(ROOT, "paper_2604_04696_gb300", "tools", "peaks_probe.cu")
+        exe = os.path.join(tempfile.gettempdir(), "gpir_peaks_probe")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        return subprocess.run([exe]).returncode
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
@@ -413,6 +453,8 @@ def main():
     clocks = Clocks(local)
     ms, clk = wl.time_steps(path, args.steps, args.warmup, barrier=barrier, clocks=clocks)
     exact = wl.check_sample() if rank == 0 else None
+    ktimes, kcount = wl.kernel_times(path, max(3, min(args.steps, 10)))
+    dom = max(ktimes, key=lambda k: ktimes[k] * kcount[k])
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -435,9 +477,12 @@ def main():
         "data": "synthetic", "config": cfg_dict(args.workload, w, PATH_NAMES[path], variant),
         "db_gbs": db_bytes / (ms / 1e3) / 1e9, "alg_gbs": alg / (ms / 1e3) / 1e9,
         "bit_exact_sample": exact,
-        "roofline": roofline(path, w, ms, peaks, args.workload),
+        "roofline": kernel_roofline(dom, w, ktimes[dom], peaks, args.workload),
+        "step_roofline": roofline(path, w, ms, peaks, args.workload),
+        "kernels": {k: {"ms": v, "launches_per_step": kcount[k], "share": v * kcount[k] / sum(
+            ktimes[x] * kcount[x] for x in ktimes)} for k, v in ktimes.items()},
         "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * sum(kcount.values()),
         "clocks": clk,
         "paths": {PATH_NAMES[p]: {"ms": v["ms"], "queries_s": w["B"] / (v["ms"] / 1e3), "variant": v["variant"]}
                   for p, v in per_path.items()},
@@ -450,10 +495,12 @@ def main():
             for b in (1, 8, 32, 128, 256):
                 ws = workload_shape("c3_sweep", b)
                 wk = GpuWorkload(g, torch, ws, mask)
-                g.gpir_autotune(wk.h, b, wk.ct, wk.out, path, wk.stream)
-                mss, _ = wk.time_steps(path, 10, 3)
-                sweep.append({"batch": b, "ms": mss, "queries_s": b / (mss / 1e3),
-                              "roofline_frac": roofline(path, ws, mss, peaks, "c3_sweep")["frac"]})
+                g.gpir_autotune(wk.h, b, wk.ct, wk.out, 0, wk.stream)     # fastest path and tile for b
+                chosen = g.gpir_selected_path(wk.h, b)
+                mss, _ = wk.time_steps(0, 10, 3)
+                sweep.append({"batch": b, "path": PATH_NAMES.get(chosen, str(chosen)), "ms": mss,
+                              "queries_s": b / (mss / 1e3),
+                              "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
         line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "

@@ -160,14 +160,19 @@ int gpir_sync(void *stream, uint32_t timeout_ms);
  * after a warm-up) for `batch` clients against this database, using the
  * caller's device buffers ct_dev / out_dev (layouts as in gpir_rowsel_batch;
  * out_dev is overwritten), and remember the fastest for (path, batch); later
- * calls with that batch use it. Synchronizes `stream`. `*variant_out` (may be
- * NULL) receives the chosen variant id. */
+ * calls with that batch use it. With path == GPIR_PATH_AUTO every prepared
+ * path is tuned and the fastest path is also remembered, so later
+ * GPIR_PATH_AUTO calls with that batch use it. Synchronizes `stream`.
+ * `*variant_out` (may be NULL) receives the chosen variant id. */
 int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                   uint32_t *out_dev, int path, void *stream, int *variant_out);
 
 /* Number of kernel variants compiled for `path` and the id in use for a
  * shape (-1 if none chosen yet). Host-only. */
 int gpir_num_variants(int path);
+/* The path GPIR_PATH_AUTO resolves to for `batch` clients (tuned, else the
+ * static rule: tensor cores from 8 clients up when prepared). Host-only. */
+int gpir_selected_path(const gpir_db_t *db, uint32_t batch);
 int gpir_selected_variant(const gpir_db_t *db, uint32_t batch, int path);
 /* Force a variant for (path, batch, D0, D1) of this database (testing). */
 int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant);
@@ -205,6 +210,18 @@ int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_
 #define GPIR_NOALLOC_SCRATCH_BYTES (64u << 20)
 int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                               uint32_t *out_dev, void *stream);
+
+/* Tracing (the paper reports per-kernel device times, Sec. 5.1.2): when
+ * enabled, each kernel the library launches is bracketed by CUDA events on
+ * its launch stream. gpir_trace_read waits for the recorded launches, copies
+ * up to max_records (name, milliseconds) pairs in launch order, sets *count,
+ * and clears the log. Off by default; a disabled trace costs nothing. */
+typedef struct gpir_trace_record {
+  char name[32];
+  float ms;
+} gpir_trace_record_t;
+int gpir_trace_enable(int on);
+int gpir_trace_read(gpir_trace_record_t *out, uint32_t max_records, uint32_t *count);
 
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return

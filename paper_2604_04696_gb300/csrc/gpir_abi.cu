@@ -147,10 +147,19 @@ int pick_variant(const gpir_db *db, uint32_t batch, int path) {
   return -1;
 }
 
-static int resolve_path(const gpir_db *db, int path) {
+// GPIR_PATH_AUTO: the path the autotuner measured fastest for this batch size,
+// else a static choice: tensor cores once a batch fills a 32-row tile well
+// (batch >= 8), CUDA cores below that (one client wastes 15/16 of an MMA tile).
+static int resolve_path(const gpir_db *db, int path, uint32_t batch) {
   if (path == GPIR_PATH_AUTO) {
-    if (db->path_mask & GPIR_PATH_TC) return GPIR_PATH_TC;
-    if (db->path_mask & GPIR_PATH_CUDACORE) return GPIR_PATH_CUDACORE;
+    {
+      std::lock_guard<std::mutex> lk(*db->mu);
+      auto it = db->variants->find({GPIR_PATH_AUTO, batch});
+      if (it != db->variants->end()) return it->second;
+    }
+    const bool tc = db->path_mask & GPIR_PATH_TC, cc = db->path_mask & GPIR_PATH_CUDACORE;
+    if (tc && (batch >= 8 || !cc)) return GPIR_PATH_TC;
+    if (cc) return GPIR_PATH_CUDACORE;
     if (db->path_mask & GPIR_PATH_IMMA) return GPIR_PATH_IMMA;
     return -1;
   }
@@ -319,7 +328,7 @@ size_t gpir_db_device_bytes(const gpir_db_t *db) {
 int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
                       void *stream) {
   if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
-  int p = resolve_path(db, path);
+  int p = resolve_path(db, path, batch);
   if (p == -1) return GPIR_EINVAL;
   if (p == -2) return GPIR_ENOTSUP;
   const size_t ct_bytes = (size_t)batch * db->d0 * 2 * db->params.num_limbs * db->params.n * 4;
@@ -423,9 +432,16 @@ int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant)
 int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
                   void *stream, int *variant_out) {
   if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
-  int p = resolve_path(db, path);
-  if (p == -1) return GPIR_EINVAL;
-  if (p == -2) return GPIR_ENOTSUP;
+  int paths[3], np = 0;
+  if (path == GPIR_PATH_AUTO) {
+    for (int p : {GPIR_PATH_CUDACORE, GPIR_PATH_IMMA, GPIR_PATH_TC})
+      if (db->path_mask & p) paths[np++] = p;
+  } else {
+    int p = resolve_path(db, path, batch);
+    if (p == -1) return GPIR_EINVAL;
+    if (p == -2) return GPIR_ENOTSUP;
+    paths[np++] = p;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return GPIR_ECUDA;
@@ -433,40 +449,59 @@ int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, u
     cudaEventDestroy(e0);
     return GPIR_ECUDA;
   }
-  int best = -1;
+  int best_path = -1, best_v = -1;
   float best_ms = 1e30f;
-  const int nv = num_variants(p);
-  for (int v = 0; v < nv; ++v) {
-    int rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);  // warm-up (and support check)
-    if (rc != GPIR_OK) continue;
-    float tot = 0.f;
-    bool okv = true;
-    for (int rep = 0; rep < 3 && okv; ++rep) {
-      cudaEventRecord(e0, s);
-      rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);
-      cudaEventRecord(e1, s);
-      if (rc != GPIR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-        okv = false;
-        break;
+  for (int pi = 0; pi < np; ++pi) {
+    const int p = paths[pi];
+    int pv = -1;
+    float pv_ms = 1e30f;
+    const int nv = num_variants(p);
+    for (int v = 0; v < nv; ++v) {
+      int rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);  // warm-up (and support check)
+      if (rc != GPIR_OK) continue;
+      float tot = 0.f;
+      bool okv = true;
+      for (int rep = 0; rep < 3 && okv; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = dispatch(db, batch, ct_dev, out_dev, p, v, s);
+        cudaEventRecord(e1, s);
+        if (rc != GPIR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          okv = false;
+          break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tot += ms;
       }
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      tot += ms;
+      if (okv && tot < pv_ms) {
+        pv_ms = tot;
+        pv = v;
+      }
     }
-    if (okv && tot < best_ms) {
-      best_ms = tot;
-      best = v;
+    if (pv >= 0) {
+      std::lock_guard<std::mutex> lk(*db->mu);
+      (*db->variants)[{p, batch}] = pv;
+    }
+    if (pv >= 0 && pv_ms < best_ms) {
+      best_ms = pv_ms;
+      best_path = p;
+      best_v = pv;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best < 0) return GPIR_ENOTSUP;
-  {
+  if (best_path < 0) return GPIR_ENOTSUP;
+  if (path == GPIR_PATH_AUTO) {
     std::lock_guard<std::mutex> lk(*db->mu);
-    (*db->variants)[{p, batch}] = best;
+    (*db->variants)[{GPIR_PATH_AUTO, batch}] = best_path;
   }
-  if (variant_out) *variant_out = best;
+  if (variant_out) *variant_out = best_v;
   return GPIR_OK;
+}
+
+int gpir_selected_path(const gpir_db_t *db, uint32_t batch) {
+  if (!db) return -1;
+  return resolve_path(db, GPIR_PATH_AUTO, batch);
 }
 
 int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_t seed, uint64_t tag,

@@ -187,7 +187,9 @@ int launch_cc(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *o
     if (e != cudaSuccess) return set_cuda_error(e);
     attr_done = true;
   }
+  const int tr = trace_begin("rowsel_cc", stream);
   rowsel_cc_kernel<C><<<(unsigned)grid, C::THREADS, C::SMEM, stream>>>(ct_map, db_map, out, p);
+  trace_end(tr, stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }

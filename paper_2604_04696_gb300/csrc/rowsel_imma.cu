@@ -263,7 +263,9 @@ int rowsel_imma_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, ui
     if (e != cudaSuccess) return set_cuda_error(e);
     attr_done = true;
   }
+  const int tr = trace_begin("rowsel_imma", stream);
   rowsel_imma_kernel<<<(unsigned)grid, THREADS, SMEM, stream>>>(ct_map, db_map, out, p);
+  trace_end(tr, stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }

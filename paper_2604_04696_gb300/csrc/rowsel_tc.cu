@@ -672,11 +672,15 @@ int tc_launch_jobs(const gpir_job_t *jobs, uint32_t njobs, uint8_t *ws, const si
   }
   tp.units = units;
   for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_limb(prm.primes[l]);
+  int tr = trace_begin("tc_ingest", stream);
   tc_ingest_kernel<<<(unsigned)blocks, INGEST_THREADS, INGEST_SMEM, stream>>>(ip);
+  trace_end(tr, stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e);
   const int grid = (int)std::min<uint64_t>((uint64_t)sm_count(), units);
+  tr = trace_begin("tc_gemm", stream);
   tc_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, stream>>>(tp);
+  trace_end(tr, stream);
   e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }

@@ -40,6 +40,10 @@ class GpirError(RuntimeError):
         super().__init__("%s failed: %s (%d)%s" % (what, _strerror(code), code, _cuda_detail(code)))
 
 
+class gpir_trace_record_t(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_float)]
+
+
 class gpir_job_t(ctypes.Structure):
     _fields_ = [("db", ctypes.c_void_p), ("batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("ct", ctypes.c_void_p), ("out", ctypes.c_void_p)]
@@ -68,8 +72,11 @@ def _load():
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
         "gpir_selected_variant": (I, [P, U32, I]),
+        "gpir_selected_path": (I, [P, U32]),
         "gpir_set_variant": (I, [P, U32, I, I]),
         "gpir_fill_uniform": (I, [P, U64, U64, U64, U64, P, U64, P]),
+        "gpir_trace_enable": (I, [I]),
+        "gpir_trace_read": (I, [ctypes.POINTER(gpir_trace_record_t), U32, ctypes.POINTER(U32)]),
         "gpir_strerror": (ctypes.c_char_p, [I]),
         "gpir_last_cuda_error": (ctypes.c_char_p, []),
         "gpir_version": (I, []),
@@ -215,6 +222,10 @@ def gpir_selected_variant(db, batch, path):
     return lib.gpir_selected_variant(db, int(batch), int(path))
 
 
+def gpir_selected_path(db, batch):
+    return lib.gpir_selected_path(db, int(batch))
+
+
 def gpir_set_variant(db, batch, path, variant):
     return _check(lib.gpir_set_variant(db, int(batch), int(path), int(variant)), "gpir_set_variant")
 
@@ -222,6 +233,18 @@ def gpir_set_variant(db, batch, path, variant):
 def gpir_fill_uniform(dst_dev, count, start, seed, tag, params, inner, stream=None):
     return _check(lib.gpir_fill_uniform(_ptr(dst_dev), int(count), int(start), int(seed), int(tag), params,
                                         int(inner), _stream(stream)), "gpir_fill_uniform")
+
+
+def gpir_trace_enable(on=True):
+    return _check(lib.gpir_trace_enable(1 if on else 0), "gpir_trace_enable")
+
+
+def gpir_trace_read(max_records=4096):
+    """[(kernel name, device ms)] of the launches since the last read (waits for them)."""
+    buf = (gpir_trace_record_t * max_records)()
+    n = ctypes.c_uint32(0)
+    _check(lib.gpir_trace_read(buf, max_records, ctypes.byref(n)), "gpir_trace_read")
+    return [(buf[i].name.decode(), float(buf[i].ms)) for i in range(n.value)]
 
 
 def gpir_strerror(code):

@@ -242,3 +242,24 @@ def test_argument_errors(g):
         assert ei.value.code == g.GPIR_EINVAL
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("B", [1, 12])
+def test_auto_path_after_autotune(g, B):
+    """GPIR_PATH_AUTO after tuning every prepared path: valid choice, same bits."""
+    from tests.gpu_util import DbHandle, to_dev, to_host, make_problem
+    primes = synth.PRIMES_28
+    D0, D1, L, N = 70, 40, 2, 128
+    ct, db = make_problem(600 + B, B, D0, D1, L, N, primes)
+    want = oracle.rowsel(ct, db, list(primes))
+    h = DbHandle(g, db, N, primes, path_mask=0)
+    try:
+        import torch
+        ct_d = to_dev(ct)
+        out = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        g.gpir_autotune(h.h, B, ct_d, out, 0)
+        assert g.gpir_selected_path(h.h, B) in (1, 2, 4)
+        got = to_host(h.rowsel(ct_d, B, 0))
+        assert np.array_equal(got, want)
+    finally:
+        h.close()
