@@ -519,6 +519,403 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
   }
 }
 
+// ---- fused persistent kernel: ingest warps + GEMM warps in one launch ------
+//
+// The ciphertexts still arrive p-major, but their digit tiles never go to HBM.
+// Work is cut into entries E = (8-slot group g, m-block mb). In every CTA,
+// eight ingest warps claim ingest tasks (E, k-chunk) in increasing order from
+// a global counter: one TMA box brings the raw residues of 8 slots x 32 rows x
+// 64 k, the warps split them into digit tiles and store them into a ring of R
+// entries in global memory (sized to stay in L2), then count the task into
+// ready[E % R]. The GEMM warps claim units (E, slot, n-block) in increasing
+// order from a second counter; the producer waits until ready[E % R] shows
+// every k-chunk of entry E before bulk-copying its tiles, and an epilogue
+// thread counts the unit into consumed[E % R] once its MMAs have read them.
+// An ingest task for E first waits until the previous occupant E - R of its
+// ring entry is fully consumed. Because both sides claim in increasing E and
+// only running CTAs hold claims, the smallest unfinished entry can always
+// progress (its only dependency lies R entries back): no deadlock, whatever
+// number of CTAs is resident. Counters are monotonic and zeroed before the
+// launch. Unit ids travel producer -> MMA thread -> epilogue through shared
+// memory with the stage and accumulator barriers. All waits are bounded.
+
+constexpr int FSTAGES = 3;
+constexpr int F_EPI_WARPS = 8;
+constexpr int F_INGEST_WARPS = 8;
+constexpr int FUSED_THREADS = 64 + 32 * F_EPI_WARPS + 32 * F_INGEST_WARPS;   // 576
+constexpr int F_RAW_BYTES = 16 * KCHUNK * 2 * 8 * 4;                         // 64 KB raw box
+constexpr size_t FUSED_SMEM = 1024 + (size_t)FSTAGES * STAGE_BYTES + F_RAW_BYTES + 256;
+constexpr uint64_t kNoUnit = ~0ull;
+
+struct FusedParams {
+  uint32_t L, N, M, d0, d1, mblk, nblk, kch;
+  uint32_t R, gpl;                      // ring entries; 8-slot groups per limb
+  uint64_t n_entries, upe, n_units, n_tasks;
+  const uint16_t *b_tiles;
+  uint32_t *out;
+  uint8_t *ring;                        // [R][8 slots][kch] x 16 KB
+  uint32_t *ready, *consumed;           // [R] each
+  unsigned long long *ctr;              // [0] next unit, [1] next ingest task
+  unsigned int *err;
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
+  TcLimb limb[GPIR_MAX_LIMBS];
+};
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
+}
+
+__global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *rawbuf = smem + FSTAGES * STAGE_BYTES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbuf + F_RAW_BYTES);
+  uint64_t *empty = full + FSTAGES;
+  uint64_t *acc_full = empty + FSTAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *raw_bar = acc_empty + 2;
+  uint64_t *stage_unit = raw_bar + 1;                 // [FSTAGES]
+  uint64_t *acc_unit = stage_unit + FSTAGES;          // [2]
+  uint64_t *task_slot = acc_unit + 2;                 // claimed ingest task
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(task_slot + 1);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < FSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 2);      // the MMA commit + the MMA thread's arrive after writing acc_unit
+      mbar_init(&acc_empty[b], F_EPI_WARPS);
+    }
+    mbar_init(raw_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto wait = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      if (mbar_try_wait(bar, parity)) return true;
+      if ((n & 63u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, code);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  // Bounded wait for a global counter to reach `target`.
+  auto wait_count = [&](const uint32_t *ctr, uint32_t target) -> bool {
+    if (ld_acquire(ctr) >= target) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      __nanosleep(64);
+      if (ld_acquire(ctr) >= target) return true;
+      if ((n & 15u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, (unsigned int)kErrQueueWait);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  auto slot_valid = [&](uint64_t E, uint32_t s) -> bool {
+    const uint32_t g = (uint32_t)(E / p.mblk);
+    return (g % p.gpl) * 8 + s < p.N;
+  };
+
+  if (warp == 0) {
+    // ---------------- producer: claims units ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0;
+      bool ok = true;
+      for (;;) {
+        const uint64_t u = atomicAdd(&p.ctr[0], 1ull);
+        if (u >= p.n_units) break;
+        const uint64_t E = u / p.upe;
+        const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+        if (!slot_valid(E, sl)) {                      // no slot behind this unit (N < 8)
+          atomicAdd(&p.consumed[E % p.R], 1u);
+          continue;
+        }
+        const uint32_t g = (uint32_t)(E / p.mblk);
+        const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
+        if (!(ok = wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch)))) break;
+        fence_proxy_async_global();
+        const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)A_TILE_BYTES;
+        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
+        for (uint32_t kc = 0; kc < p.kch; ++kc) {
+          if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
+          stage_unit[st] = u;   // read by the MMA thread on the unit's first stage
+          uint8_t *sa = smem + st * STAGE_BYTES;
+          mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+          bulk_g2s(sa, a_src + (uint64_t)kc * A_TILE_BYTES, A_TILE_BYTES, &full[st]);
+          bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st]);
+          if (++st == FSTAGES) {
+            st = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      // end of work: one empty stage carrying the sentinel
+      if (ok && wait(&empty[st], ph ^ 1u, kErrTmaWait)) {
+        stage_unit[st] = kNoUnit;
+        mbar_arrive(&full[st]);
+      } else {
+        for (int s2 = 0; s2 < FSTAGES; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, buf = 0;
+      uint32_t aph[2] = {0, 0};
+      bool ok = true;
+      const uint32_t kgroups = (p.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
+      for (;;) {
+        // first stage of the next unit (or the sentinel)
+        if (!(ok = wait(&full[st], ph, kErrTmaWait))) break;
+        const uint64_t u = stage_unit[st];
+        if (u == kNoUnit) {
+          if ((ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
+            acc_unit[buf] = kNoUnit;
+            mbar_arrive_cnt(&acc_full[buf], 2);
+          }
+          break;
+        }
+        bool first = true;
+        for (uint32_t gi = 0; gi < kgroups && ok; ++gi) {
+          if (!(ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) break;
+          tc_fence_after();
+          const uint32_t tmem_d = tmem_base + buf * 256;
+          const uint32_t c0 = gi * KGROUP_CHUNKS;
+          const uint32_t c1 = min(p.kch, c0 + KGROUP_CHUNKS);
+          for (uint32_t kc = c0; kc < c1; ++kc) {
+            if (!first && !(ok = wait(&full[st], ph, kErrTmaWait))) break;
+            first = false;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sb = sa + A_TILE_BYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < KCHUNK / 16; ++k16)
+              mma_bf16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32), (kc > c0 || k16 > 0) ? 1u : 0u);
+            mma_commit(&empty[st]);
+            if (++st == FSTAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          acc_unit[buf] = u | ((gi + 1 == kgroups) ? (1ull << 63) : 0ull);   // unit id, top bit: last group
+          mma_commit(&acc_full[buf]);
+          mbar_arrive(&acc_full[buf]);
+          aph[buf] ^= 1u;
+          buf ^= 1u;
+        }
+        if (!ok) break;
+      }
+      if (!ok)
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&acc_full[b], aph[b], nullptr, 0);
+    }
+  } else if (warp < 2 + F_EPI_WARPS) {
+    // ---------------- epilogue (8 warps) ----------------
+    constexpr int CHUNKS = 8 / (F_EPI_WARPS / 4);
+    const uint32_t quarter = warp & 3;
+    const int jbase = ((warp - 2) >> 2) * CHUNKS;
+    const int u = lane >> 3, m_lo = lane & 7;
+    const int m_local = quarter * 8 + m_lo;
+    const bool odd = (u & 1) != 0, high = (u & 2) != 0;
+    const bool signaller = (warp == 2 && lane == 0);
+    uint32_t buf = 0;
+    uint32_t aph[2] = {0, 0};
+    uint32_t res[2 * CHUNKS];
+#pragma unroll
+    for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
+    for (;;) {
+      if (!wait(&acc_full[buf], aph[buf], kErrMmaWait)) break;
+      tc_fence_after();
+      const uint64_t tag = acc_unit[buf];
+      if (tag == kNoUnit) break;
+      const uint64_t un = tag & ~(1ull << 63);
+      const bool last = (tag >> 63) != 0;
+      const uint64_t E = un / p.upe;
+      const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
+      const TcLimb &lm = p.limb[l];
+      if (last && signaller) atomicAdd(&p.consumed[E % p.R], 1u);   // its ring tiles are no longer needed
+      const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
+      const uint32_t taddr = tmem_base + ((quarter * 32u) << 16) + buf * 256 + jbase * 32;
+#pragma unroll
+      for (int j = 0; j < CHUNKS; ++j) {
+        uint32_t d[32];
+        tmem_ld32(taddr + j * 32, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t P[4];
+#pragma unroll
+          for (int ww = 0; ww < 4; ++ww) {
+            const int n8 = h * 4 + ww;
+            const int32_t b0 = __float_as_int(__uint_as_float(d[n8 * 4 + 0]) + 12582912.0f);
+            const int32_t b1 = __float_as_int(__uint_as_float(d[n8 * 4 + 1]) + 12582912.0f);
+            const int32_t b2 = __float_as_int(__uint_as_float(d[n8 * 4 + 2]) + 12582912.0f);
+            const int32_t b3 = __float_as_int(__uint_as_float(d[n8 * 4 + 3]) + 12582912.0f);
+            P[ww] = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3;
+          }
+          int64_t k0 = odd ? P[1] : P[0], k1 = odd ? P[3] : P[2];
+          const int64_t s0 = odd ? P[0] : P[1], s1 = odd ? P[2] : P[3];
+          k0 += __shfl_xor_sync(0xffffffffu, s0, 8);
+          k1 += __shfl_xor_sync(0xffffffffu, s1, 8);
+          int64_t keep = high ? k1 : k0;
+          const int64_t send = high ? k0 : k1;
+          keep += __shfl_xor_sync(0xffffffffu, send, 16);
+          const uint32_t rr = reduce64((uint64_t)(keep - lm.kfix + (int64_t)lm.off), lm.q, lm.mu);
+          uint32_t &acc = res[j * 2 + h];
+          acc += rr;
+          acc = acc >= lm.q ? acc - lm.q : acc;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      aph[buf] ^= 1u;
+      buf ^= 1u;
+      if (last) {
+        const uint32_t m = mb * MROWS + m_local;
+        if (m < p.M) {
+          const uint32_t c = m >> 1, rr = m & 1;
+#pragma unroll
+          for (int j = 0; j < CHUNKS; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t n = nb * NCOLS + (jbase + j) * 8 + h * 4 + u;
+              if (n < p.d1) p.out[((((uint64_t)c * p.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
+      }
+    }
+  } else {
+    // ---------------- ingest (8 warps, 256 threads) ----------------
+    // Thread (m_local, position cp) reads the 8 slots' residues of row
+    // m_local for k octet k_oct = cp ^ (m_local % 8) and writes, for every
+    // digit u and slot, the 16-byte chunk at position cp of tile row
+    // m_hi*32 + u*8 + m_lo (the swizzled place of that k octet), so each warp
+    // store covers 8 half rows (64 contiguous bytes each) of one tile.
+    const int iw = warp - (2 + F_EPI_WARPS);
+    const int it = iw * 32 + lane;
+    const int m_hi = iw >> 1, cp = (iw & 1) * 4 + (lane >> 3), m_lo = lane & 7;
+    const int m_local = m_hi * 8 + m_lo;
+    const int cc = m_local >> 1, rp = m_local & 1, k_oct = cp ^ m_lo;
+    // Every exit decision is made uniformly for the 256 ingest threads (a
+    // value thread 0 publishes before a named barrier, or a barrier AND), so
+    // no thread can leave while the others wait at the next named barrier.
+    uint32_t rph = 0;
+    bool issued = false;
+    for (;;) {
+      if (it == 0) {
+        const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
+        *task_slot = (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
+      const uint64_t tk = *task_slot;
+      if (tk == kNoUnit) break;
+      const uint64_t E = tk / p.kch;
+      const uint32_t kc = (uint32_t)(tk % p.kch);
+      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");   // everyone has read task_slot
+      if (it == 0) {
+        // the ring entry's previous occupant must be fully consumed
+        if (E < p.R || wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe))) {
+          mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
+          tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK), (int)(mb * (MROWS / 2)));
+          issued = true;
+          *task_slot = tk;
+        } else {
+          *task_slot = kNoUnit;
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
+      if (*task_slot == kNoUnit) break;
+      uint32_t got = wait(raw_bar, rph, kErrTmaWait) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(got)
+          : "r"(got), "n"(32 * F_INGEST_WARPS)
+          : "memory");
+      if (!got) break;
+      rph ^= 1u;
+      if (it == 0) issued = false;
+      const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbuf);
+      uint32_t v[8][8];   // [kk][slot]
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int row = (cc * KCHUNK + k_oct * 8 + kk) * 2 + rp;   // 32-byte row: 8 slots
+        const uint4 lo = raw4[row * 2], hi = raw4[row * 2 + 1];
+        v[kk][0] = lo.x; v[kk][1] = lo.y; v[kk][2] = lo.z; v[kk][3] = lo.w;
+        v[kk][4] = hi.x; v[kk][5] = hi.y; v[kk][6] = hi.z; v[kk][7] = hi.w;
+      }
+      uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
+#pragma unroll
+      for (int sl = 0; sl < 8; ++sl) {
+        if (t0 + sl >= p.N) continue;
+        uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)A_TILE_BYTES) / 16;
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) {
+          uint4 w4;
+          w4.x = digit_bf16_bits(v[0][sl], uu) | (digit_bf16_bits(v[1][sl], uu) << 16);
+          w4.y = digit_bf16_bits(v[2][sl], uu) | (digit_bf16_bits(v[3][sl], uu) << 16);
+          w4.z = digit_bf16_bits(v[4][sl], uu) | (digit_bf16_bits(v[5][sl], uu) << 16);
+          w4.w = digit_bf16_bits(v[6][sl], uu) | (digit_bf16_bits(v[7][sl], uu) << 16);
+          tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
+        }
+      }
+      fence_proxy_async_global();
+      __threadfence();
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
+      if (it == 0) atomicAdd(&p.ready[E % p.R], 1u);
+    }
+    if (it == 0 && issued) mbar_wait_bounded(raw_bar, rph, nullptr, 0);   // let a late box land
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+}
+
 static TcLimb make_limb(uint32_t q) {
   TcLimb t;
   t.q = q;
@@ -541,7 +938,7 @@ static TcLimb make_limb(uint32_t q) {
 
 }  // namespace
 
-int rowsel_tc_num_variants() { return 1; }
+int rowsel_tc_num_variants() { return 2; }   // 0: fused single launch, 1: two-pass
 int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
 
 int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
@@ -720,18 +1117,95 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
   return GPIR_OK;
 }
 
+constexpr size_t kRingBytes = 40ull << 20;   // digit-tile ring of the fused kernel: stays in L2
+
+std::mutex g_fused_attr_mu;
+bool g_fused_attr_done[64];
+
+// One RowSel problem through the fused persistent kernel (ingest warps and
+// GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
+int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, cudaStream_t stream) {
+  if (!db->db_digits) return GPIR_ENOTSUP;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(g_fused_attr_mu);
+    if (!g_fused_attr_done[dev]) {
+      e = cudaFuncSetAttribute(tc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      g_fused_attr_done[dev] = true;
+    }
+  }
+  const gpir_params &prm = db->params;
+  const uint32_t L = prm.num_limbs, N = prm.n;
+  const TcShape sh = tc_shape(db, batch);
+  FusedParams fp;
+  memset(&fp, 0, sizeof(fp));
+  fp.L = L;
+  fp.N = N;
+  fp.M = sh.M;
+  fp.d0 = db->d0;
+  fp.d1 = db->d1;
+  fp.mblk = sh.mblk;
+  fp.nblk = sh.nblk;
+  fp.kch = sh.kch;
+  fp.gpl = (N + 7) / 8;
+  fp.n_entries = (uint64_t)fp.gpl * L * sh.mblk;
+  fp.upe = 8ull * sh.nblk;
+  fp.n_units = fp.n_entries * fp.upe;
+  fp.n_tasks = fp.n_entries * sh.kch;
+  const size_t entry_bytes = (size_t)8 * sh.kch * A_TILE_BYTES;
+  uint64_t R = kRingBytes / entry_bytes;
+  if (R < 2) R = 2;
+  if (R > fp.n_entries) R = fp.n_entries;
+  fp.R = (uint32_t)R;
+  const size_t ring_bytes = (size_t)R * entry_bytes;
+  const size_t flag_bytes = ((size_t)8 * R + 16 + 255) & ~(size_t)255;
+  uint8_t *ws = nullptr;
+  int rc = stream_workspace(stream, ring_bytes + flag_bytes, &ws);
+  if (rc != GPIR_OK) return rc;
+  fp.ring = ws;
+  fp.ctr = reinterpret_cast<unsigned long long *>(ws + ring_bytes);
+  fp.ready = reinterpret_cast<uint32_t *>(ws + ring_bytes + 16);
+  fp.consumed = fp.ready + R;
+  e = cudaMemsetAsync(ws + ring_bytes, 0, flag_bytes, stream);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  {
+    const uint64_t dims[5] = {N, L, 2, db->d0, batch};
+    const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
+                             (uint64_t)db->d0 * 2 * L * N * 4};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)KCHUNK, (uint32_t)(MROWS / 2)};
+    rc = encode_tiled_u32(&fp.ct_map, ct, 5, dims, str, box);
+    if (rc != GPIR_OK) return rc;
+  }
+  fp.b_tiles = db->db_digits;
+  fp.out = out;
+  fp.err = device_error_word();
+  for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
+  const int grid = sm_count();
+  const int tr = trace_begin("tc_fused", stream);
+  tc_fused_kernel<<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+  trace_end(tr, stream);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
 }  // namespace
 
 int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
                      cudaStream_t stream) {
-  (void)variant;
-  gpir_job_t job;
-  job.db = db;
-  job.batch = batch;
-  job.reserved = 0;
-  job.ct = ct;
-  job.out = out;
-  return rowsel_tc_multi(&job, 1, stream);
+  if (variant == 1) {
+    gpir_job_t job;
+    job.db = db;
+    job.batch = batch;
+    job.reserved = 0;
+    job.ct = ct;
+    job.out = out;
+    return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
+  }
+  return tc_launch_fused(db, batch, ct, out, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {
