@@ -222,6 +222,14 @@ typedef struct gpir_trace_record {
 } gpir_trace_record_t;
 int gpir_trace_enable(int on);
 int gpir_trace_read(gpir_trace_record_t *out, uint32_t max_records, uint32_t *count);
+/* Wait-cycle counters of the last fused tensor-core launch made while tracing
+ * was on (SM clock cycles summed over CTAs, one counting thread per role):
+ * [0] producer waiting for ingested tiles, [1] producer waiting for a free
+ * stage, [2] MMA waiting for operands, [3] MMA waiting for the epilogue,
+ * [4] epilogue waiting for MMAs, [5] ingest waiting for a ring entry,
+ * [6] ingest waiting for its TMA box, [7] ingest converting, [8] kernel
+ * cycles per CTA. Tracing makes that launch synchronous. */
+int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t *count);
 
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return

@@ -93,6 +93,8 @@ int rowsel_tc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
 // Tracing hooks: trace_begin returns -1 (and records nothing) when disabled.
 int trace_begin(const char *name, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
+bool trace_enabled();
+void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 
 int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs);

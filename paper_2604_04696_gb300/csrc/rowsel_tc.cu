@@ -37,6 +37,7 @@
 // accumulators, so draining overlaps the next group's MMAs) and write the
 // canonical residues in the p-major output layout.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -557,8 +558,38 @@ struct FusedParams {
   uint32_t *ready, *consumed;           // [R] each
   unsigned long long *ctr;              // [0] next unit, [1] next ingest task
   unsigned int *err;
+  unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
   CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
   TcLimb limb[GPIR_MAX_LIMBS];
+};
+
+
+// Two bf16 digits u of x0, x1 (x' = x + 0x808080 precomputed) packed as
+// bf16x2: PRMT puts byte u of x' under the exponent of 2^23, so the fp32 is
+// 2^23 + byte; subtracting 2^23 + 128 (2^23 for the top digit) leaves the
+// digit, exact in bf16.
+__device__ __forceinline__ uint32_t digits2_bf16(uint32_t xp0, uint32_t xp1, int u) {
+  const float off = u < 3 ? 8388736.0f : 8388608.0f;
+  const float f0 = __int_as_float(__byte_perm(xp0, 0x4B000000u, 0x7650u + u)) - off;
+  const float f1 = __int_as_float(__byte_perm(xp1, 0x4B000000u, 0x7650u + u)) - off;
+  __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Wait-cycle counters of the fused kernel (summed over CTAs; one thread per
+// role counts), compiled in only for the traced instantiation and read
+// through gpir_trace_counters.
+enum FusedCounter {
+  kPWaitReady = 0,    // producer waits for the ingest (ring entry not ready)
+  kPWaitEmpty,        // producer waits for a free smem stage (MMA behind)
+  kMWaitFull,         // MMA thread waits for operands
+  kMWaitAccEmpty,     // MMA thread waits for the epilogue to drain
+  kEWaitAccFull,      // epilogue waits for the MMAs
+  kIWaitConsumed,     // ingest waits for a ring entry to be released
+  kIWaitBox,          // ingest waits for its TMA box
+  kIBusy,             // ingest converting and storing
+  kCtaCycles,         // whole kernel, per CTA
+  kNumFusedCounters
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
@@ -575,6 +606,7 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
 }
 
+template <bool PROF>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -651,6 +683,18 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     const uint32_t g = (uint32_t)(E / p.mblk);
     return (g % p.gpl) * 8 + s < p.N;
   };
+  uint64_t pc[PROF ? kNumFusedCounters : 1];
+#pragma unroll
+  for (int i = 0; i < (PROF ? kNumFusedCounters : 1); ++i) pc[i] = 0;
+  const uint64_t kstart = PROF ? clock64() : 0;
+  // time a wait into counter `k` (traced instantiation only)
+#define FUSED_TIMED(k, expr)                              \
+  ([&]() {                                                 \
+    const uint64_t _t0 = PROF ? clock64() : 0;             \
+    const bool _r = (expr);                                \
+    if (PROF) pc[PROF ? (k) : 0] += clock64() - _t0;       \
+    return _r;                                             \
+  }())
 
   if (warp == 0) {
     // ---------------- producer: claims units ----------------
@@ -668,12 +712,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         }
         const uint32_t g = (uint32_t)(E / p.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        if (!(ok = wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch)))) break;
+        if (!(ok = FUSED_TIMED(kPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
         fence_proxy_async_global();
         const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)A_TILE_BYTES;
         const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
         for (uint32_t kc = 0; kc < p.kch; ++kc) {
-          if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
+          if (!(ok = FUSED_TIMED(kPWaitEmpty, wait(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
           stage_unit[st] = u;   // read by the MMA thread on the unit's first stage
           uint8_t *sa = smem + st * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
@@ -703,7 +747,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       const uint32_t kgroups = (p.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
       for (;;) {
         // first stage of the next unit (or the sentinel)
-        if (!(ok = wait(&full[st], ph, kErrTmaWait))) break;
+        if (!(ok = FUSED_TIMED(kMWaitFull, wait(&full[st], ph, kErrTmaWait)))) break;
         const uint64_t u = stage_unit[st];
         if (u == kNoUnit) {
           if ((ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
@@ -714,13 +758,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         }
         bool first = true;
         for (uint32_t gi = 0; gi < kgroups && ok; ++gi) {
-          if (!(ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) break;
+          if (!(ok = FUSED_TIMED(kMWaitAccEmpty, wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait)))) break;
           tc_fence_after();
           const uint32_t tmem_d = tmem_base + buf * 256;
           const uint32_t c0 = gi * KGROUP_CHUNKS;
           const uint32_t c1 = min(p.kch, c0 + KGROUP_CHUNKS);
           for (uint32_t kc = c0; kc < c1; ++kc) {
-            if (!first && !(ok = wait(&full[st], ph, kErrTmaWait))) break;
+            if (!first && !(ok = FUSED_TIMED(kMWaitFull, wait(&full[st], ph, kErrTmaWait)))) break;
             first = false;
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
@@ -761,7 +805,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
 #pragma unroll
     for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
     for (;;) {
-      if (!wait(&acc_full[buf], aph[buf], kErrMmaWait)) break;
+      bool okw;
+      if (warp == 2 && lane == 0) okw = FUSED_TIMED(kEWaitAccFull, wait(&acc_full[buf], aph[buf], kErrMmaWait));
+      else okw = wait(&acc_full[buf], aph[buf], kErrMmaWait);
+      if (!okw) break;
       tc_fence_after();
       const uint64_t tag = acc_unit[buf];
       if (tag == kNoUnit) break;
@@ -857,7 +904,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");   // everyone has read task_slot
       if (it == 0) {
         // the ring entry's previous occupant must be fully consumed
-        if (E < p.R || wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe))) {
+        if (E < p.R || FUSED_TIMED(kIWaitConsumed, wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe)))) {
           mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
           tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK), (int)(mb * (MROWS / 2)));
           issued = true;
@@ -868,7 +915,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
       if (*task_slot == kNoUnit) break;
-      uint32_t got = wait(raw_bar, rph, kErrTmaWait) ? 1u : 0u;
+      uint32_t got = (it == 0 ? FUSED_TIMED(kIWaitBox, wait(raw_bar, rph, kErrTmaWait))
+                              : wait(raw_bar, rph, kErrTmaWait)) ? 1u : 0u;
       asm volatile(
           "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
           " selp.u32 %0, 1, 0, pout;\n}"
@@ -878,14 +926,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       if (!got) break;
       rph ^= 1u;
       if (it == 0) issued = false;
+      const uint64_t tbusy = PROF ? clock64() : 0;
       const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbuf);
-      uint32_t v[8][8];   // [kk][slot]
+      uint32_t v[8][8];   // [kk][slot]: residue + 0x808080
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
         const int row = (cc * KCHUNK + k_oct * 8 + kk) * 2 + rp;   // 32-byte row: 8 slots
         const uint4 lo = raw4[row * 2], hi = raw4[row * 2 + 1];
-        v[kk][0] = lo.x; v[kk][1] = lo.y; v[kk][2] = lo.z; v[kk][3] = lo.w;
-        v[kk][4] = hi.x; v[kk][5] = hi.y; v[kk][6] = hi.z; v[kk][7] = hi.w;
+        v[kk][0] = lo.x + 0x808080u; v[kk][1] = lo.y + 0x808080u; v[kk][2] = lo.z + 0x808080u;
+        v[kk][3] = lo.w + 0x808080u; v[kk][4] = hi.x + 0x808080u; v[kk][5] = hi.y + 0x808080u;
+        v[kk][6] = hi.z + 0x808080u; v[kk][7] = hi.w + 0x808080u;
       }
       uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
 #pragma unroll
@@ -895,19 +945,31 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
 #pragma unroll
         for (int uu = 0; uu < 4; ++uu) {
           uint4 w4;
-          w4.x = digit_bf16_bits(v[0][sl], uu) | (digit_bf16_bits(v[1][sl], uu) << 16);
-          w4.y = digit_bf16_bits(v[2][sl], uu) | (digit_bf16_bits(v[3][sl], uu) << 16);
-          w4.z = digit_bf16_bits(v[4][sl], uu) | (digit_bf16_bits(v[5][sl], uu) << 16);
-          w4.w = digit_bf16_bits(v[6][sl], uu) | (digit_bf16_bits(v[7][sl], uu) << 16);
+          w4.x = digits2_bf16(v[0][sl], v[1][sl], uu);
+          w4.y = digits2_bf16(v[2][sl], v[3][sl], uu);
+          w4.z = digits2_bf16(v[4][sl], v[5][sl], uu);
+          w4.w = digits2_bf16(v[6][sl], v[7][sl], uu);
           tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
         }
       }
       fence_proxy_async_global();
-      __threadfence();
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
-      if (it == 0) atomicAdd(&p.ready[E % p.R], 1u);
+      if (it == 0) {
+        __threadfence();   // cumulative: orders the group's tile stores (seen through the barrier) before the count
+        atomicAdd(&p.ready[E % p.R], 1u);
+      }
+      if (PROF) pc[PROF ? kIBusy : 0] += clock64() - tbusy;
     }
     if (it == 0 && issued) mbar_wait_bounded(raw_bar, rph, nullptr, 0);   // let a late box land
+  }
+#undef FUSED_TIMED
+  if (PROF) {
+    // one counting thread per role: producer, MMA, epilogue warp 2, ingest thread 0
+    const bool counter = (lane == 0) && (warp <= 2 || warp == 2 + F_EPI_WARPS);
+    if (counter)
+      for (int i = 0; i < (PROF ? kNumFusedCounters : 1) - 1; ++i)
+        if (pc[i]) atomicAdd(&p.prof[i], pc[i]);
+    if (threadIdx.x == 0) atomicAdd(&p.prof[kCtaCycles], clock64() - kstart);
   }
   tc_fence_before();
   __syncthreads();
@@ -938,7 +1000,7 @@ static TcLimb make_limb(uint32_t q) {
 
 }  // namespace
 
-int rowsel_tc_num_variants() { return 2; }   // 0: fused single launch, 1: two-pass
+int rowsel_tc_num_variants() { return 4; }   // 0/2/3: fused, ring 48/24/96 MB; 1: two-pass
 int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
 
 int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
@@ -1117,14 +1179,17 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
   return GPIR_OK;
 }
 
-constexpr size_t kRingBytes = 40ull << 20;   // digit-tile ring of the fused kernel: stays in L2
+// Digit-tile ring of the fused kernel, sized against the 129 MB L2 (a tile
+// variant each, picked by the autotuner).
+constexpr size_t kRingBytes[3] = {48ull << 20, 24ull << 20, 96ull << 20};
 
 std::mutex g_fused_attr_mu;
 bool g_fused_attr_done[64];
 
 // One RowSel problem through the fused persistent kernel (ingest warps and
 // GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
-int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, cudaStream_t stream) {
+int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
+                    cudaStream_t stream) {
   if (!db->db_digits) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1133,7 +1198,9 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   {
     std::lock_guard<std::mutex> lk(g_fused_attr_mu);
     if (!g_fused_attr_done[dev]) {
-      e = cudaFuncSetAttribute(tc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+      e = cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
       if (e != cudaSuccess) return set_cuda_error(e);
       g_fused_attr_done[dev] = true;
     }
@@ -1157,12 +1224,12 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.n_units = fp.n_entries * fp.upe;
   fp.n_tasks = fp.n_entries * sh.kch;
   const size_t entry_bytes = (size_t)8 * sh.kch * A_TILE_BYTES;
-  uint64_t R = kRingBytes / entry_bytes;
+  uint64_t R = ring_target / entry_bytes;
   if (R < 2) R = 2;
   if (R > fp.n_entries) R = fp.n_entries;
   fp.R = (uint32_t)R;
   const size_t ring_bytes = (size_t)R * entry_bytes;
-  const size_t flag_bytes = ((size_t)8 * R + 16 + 255) & ~(size_t)255;
+  const size_t flag_bytes = ((size_t)8 * R + 16 + 8 * kNumFusedCounters + 255) & ~(size_t)255;
   uint8_t *ws = nullptr;
   int rc = stream_workspace(stream, ring_bytes + flag_bytes, &ws);
   if (rc != GPIR_OK) return rc;
@@ -1170,6 +1237,8 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.ctr = reinterpret_cast<unsigned long long *>(ws + ring_bytes);
   fp.ready = reinterpret_cast<uint32_t *>(ws + ring_bytes + 16);
   fp.consumed = fp.ready + R;
+  fp.prof = trace_enabled() ? reinterpret_cast<unsigned long long *>(fp.consumed + R) : nullptr;
+  if (fp.prof && ((uintptr_t)fp.prof & 7)) fp.prof = reinterpret_cast<unsigned long long *>(((uintptr_t)fp.prof + 7) & ~(uintptr_t)7);
   e = cudaMemsetAsync(ws + ring_bytes, 0, flag_bytes, stream);
   if (e != cudaSuccess) return set_cuda_error(e);
   {
@@ -1186,8 +1255,12 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
   const int grid = sm_count();
   const int tr = trace_begin("tc_fused", stream);
-  tc_fused_kernel<<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+  if (fp.prof)
+    tc_fused_kernel<true><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+  else
+    tc_fused_kernel<false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
   trace_end(tr, stream);
+  if (fp.prof) trace_counters(fp.prof, kNumFusedCounters, stream);
   e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
@@ -1205,7 +1278,8 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
   }
-  return tc_launch_fused(db, batch, ct, out, stream);
+  const size_t ring = kRingBytes[variant == 2 ? 1 : variant == 3 ? 2 : 0];
+  return tc_launch_fused(db, batch, ct, out, ring, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {

@@ -21,8 +21,24 @@ struct Rec {
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
+std::vector<unsigned long long> g_counters;   // last kernel's wait-cycle counters
 
 }  // namespace
+
+bool trace_enabled() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on;
+}
+
+// Copy a kernel's device counters to the host (synchronizes `s`).
+void trace_counters(const unsigned long long *dev, int n, cudaStream_t s) {
+  std::vector<unsigned long long> h(n, 0);
+  if (cudaMemcpyAsync(h.data(), dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_counters = h;
+  }
+}
 
 int trace_begin(const char *name, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -75,6 +91,18 @@ int gpir_trace_read(gpir_trace_record_t *out, uint32_t max_records, uint32_t *co
   gpir::g_recs.clear();
   *count = n;
   return rc;
+}
+
+int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t *count) {
+  if (!count) return GPIR_EINVAL;
+  std::lock_guard<std::mutex> lk(gpir::g_mu);
+  uint32_t n = 0;
+  for (auto v : gpir::g_counters) {
+    if (out && n < max_counters) out[n] = v;
+    ++n;
+  }
+  *count = n < max_counters ? n : max_counters;
+  return GPIR_OK;
 }
 
 }  // extern "C"

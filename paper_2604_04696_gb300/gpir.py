@@ -77,6 +77,7 @@ def _load():
         "gpir_fill_uniform": (I, [P, U64, U64, U64, U64, P, U64, P]),
         "gpir_trace_enable": (I, [I]),
         "gpir_trace_read": (I, [ctypes.POINTER(gpir_trace_record_t), U32, ctypes.POINTER(U32)]),
+        "gpir_trace_counters": (I, [ctypes.POINTER(ctypes.c_ulonglong), U32, ctypes.POINTER(U32)]),
         "gpir_strerror": (ctypes.c_char_p, [I]),
         "gpir_last_cuda_error": (ctypes.c_char_p, []),
         "gpir_version": (I, []),
@@ -245,6 +246,18 @@ def gpir_trace_read(max_records=4096):
     n = ctypes.c_uint32(0)
     _check(lib.gpir_trace_read(buf, max_records, ctypes.byref(n)), "gpir_trace_read")
     return [(buf[i].name.decode(), float(buf[i].ms)) for i in range(n.value)]
+
+
+FUSED_COUNTERS = ["producer_wait_ready", "producer_wait_empty", "mma_wait_full", "mma_wait_acc_empty",
+                  "epilogue_wait_acc_full", "ingest_wait_consumed", "ingest_wait_box", "ingest_busy", "cta_cycles"]
+
+
+def gpir_trace_counters():
+    """{name: cycles} of the last fused tensor-core launch made with tracing on."""
+    buf = (ctypes.c_ulonglong * 16)()
+    n = ctypes.c_uint32(0)
+    _check(lib.gpir_trace_counters(buf, 16, ctypes.byref(n)), "gpir_trace_counters")
+    return {FUSED_COUNTERS[i] if i < len(FUSED_COUNTERS) else str(i): int(buf[i]) for i in range(n.value)}
 
 
 def gpir_strerror(code):
