@@ -34,9 +34,9 @@ struct CcParams {
   LimbTable limbs;
 };
 
-template <int MT_, int NT_, int WM_, int WN_, int KC_, int STAGES_>
+template <int MT_, int NT_, int WM_, int WN_, int KC_, int STAGES_, int MINB_ = 1>
 struct CcCfg {
-  static constexpr int MT = MT_, NT = NT_, WM = WM_, WN = WN_, KC = KC_, STAGES = STAGES_;
+  static constexpr int MT = MT_, NT = NT_, WM = WM_, WN = WN_, KC = KC_, STAGES = STAGES_, MINB = MINB_;
   static constexpr int MB = WM * MT, NB = WN * NT, THREADS = WM * WN * 32;
   static_assert(MB % 2 == 0, "a row block holds whole ciphertexts (2 polynomials)");
   static_assert(256 % KC == 0, "reduction period must be a whole number of chunks");
@@ -48,7 +48,7 @@ struct CcCfg {
 };
 
 template <class C>
-__global__ void __launch_bounds__(C::THREADS, 1)
+__global__ void __launch_bounds__(C::THREADS, C::MINB)
     rowsel_cc_kernel(const __grid_constant__ CUtensorMap ct_map, const __grid_constant__ CUtensorMap db_map,
                      uint32_t *__restrict__ out, const CcParams p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -201,10 +201,14 @@ using V2 = CcCfg<8, 8, 2, 4, 8, 3>;   // MB=16 NB=32
 using V3 = CcCfg<8, 8, 4, 2, 8, 3>;   // MB=32 NB=16
 using V4 = CcCfg<4, 4, 2, 4, 8, 4>;   // MB=8  NB=16 : small shapes
 using V5 = CcCfg<8, 4, 4, 2, 16, 2>;  // MB=32 NB=8
+using V6 = CcCfg<4, 4, 4, 4, 8, 3, 2>;   // MB=16 NB=16, 16 warps, 2 CTAs/SM
+using V7 = CcCfg<4, 8, 4, 4, 8, 3>;      // MB=16 NB=32, 16 warps
+using V8 = CcCfg<8, 4, 4, 4, 8, 3>;      // MB=32 NB=16, 16 warps
+using V9 = CcCfg<4, 4, 2, 4, 8, 3, 3>;   // MB=8  NB=16, 8 warps, 3 CTAs/SM
 
 }  // namespace
 
-int rowsel_cc_num_variants() { return 6; }
+int rowsel_cc_num_variants() { return 10; }
 
 int rowsel_cc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1) {
   (void)d0;
@@ -223,6 +227,10 @@ int rowsel_cc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     case 3: return launch_cc<V3>(db, batch, ct, out, stream);
     case 4: return launch_cc<V4>(db, batch, ct, out, stream);
     case 5: return launch_cc<V5>(db, batch, ct, out, stream);
+    case 6: return launch_cc<V6>(db, batch, ct, out, stream);
+    case 7: return launch_cc<V7>(db, batch, ct, out, stream);
+    case 8: return launch_cc<V8>(db, batch, ct, out, stream);
+    case 9: return launch_cc<V9>(db, batch, ct, out, stream);
     default: return GPIR_EINVAL;
   }
 }
