@@ -222,13 +222,14 @@ def roofline(path_id, w, ms, peaks, workload):
     t_hbm = alg / (peaks["hbm_gbs"] * 1e9)
     traffic = None
     if path_id == 4:
-        flops = 2.0 * 16 * macs       # 16 exact bf16 digit products per modular MAC
+        flops = 2.0 * 16 * macs       # 16 exact fp16 digit products per modular MAC
         t_c = flops / (peaks["bf16_tflops"] * 1e12)
         if t_c >= t_hbm:
             a = flops / s / 1e12
             return {"bound": "tensor", "achieved": a, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": a / peaks["bf16_tflops"], "traffic": traffic,
-                    "note": "bf16 digit-product flops (16 per modular MAC) vs %s cuBLAS bf16 burst" % peaks["source"]}
+                    "note": "fp16 digit-product flops (16 per modular MAC) vs %s cuBLAS bf16 burst "
+                            "(fp16 and bf16 share one nominal dense rate)" % peaks["source"]}
     elif path_id == 2:
         ops = 2.0 * 16 * macs         # 16 u8 x u8 products per modular MAC
         imma_peak = 151.0             # TOPS, measured mma.sync m16n8k32 u8 on this GB300 pool
@@ -473,7 +474,7 @@ def main():
         "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {1: "u32 (u64 accumulate)", 2: "u8 (s32 accumulate)",
-                                       4: "bf16 digits (fp32 exact accumulate)"}[path],
+                                       4: "fp16 digits (fp32 exact accumulate)"}[path],
         "data": "synthetic", "config": cfg_dict(args.workload, w, PATH_NAMES[path], variant),
         "db_gbs": db_bytes / (ms / 1e3) / 1e9, "alg_gbs": alg / (ms / 1e3) / 1e9,
         "bit_exact_sample": exact,

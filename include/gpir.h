@@ -52,7 +52,7 @@ extern "C" {
 #define GPIR_PATH_AUTO      0  /* fastest prepared path for the shape        */
 #define GPIR_PATH_CUDACORE  1  /* 32x32->64-bit IMAD products, CUDA cores     */
 #define GPIR_PATH_IMMA      2  /* INT8 tensor cores (mma.sync u8), byte limbs */
-#define GPIR_PATH_TC        4  /* tcgen05 bf16 tensor cores, signed 8-bit
+#define GPIR_PATH_TC        4  /* tcgen05 fp16 tensor cores, signed 8-bit
                                   digits, exact fp32 partial sums            */
 #define GPIR_PATH_ALL       7
 

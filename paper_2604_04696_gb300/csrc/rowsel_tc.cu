@@ -1,4 +1,4 @@
-// RowSel on the 5th-generation tensor cores (tcgen05, bf16 operands, fp32
+// RowSel on the 5th-generation tensor cores (tcgen05, fp16 operands, fp32
 // accumulators in tensor memory), exact.
 //
 // What is computed: the per-point modular GEMM of Sec. 2.3 / Sec. 5.1 of the
@@ -7,7 +7,7 @@
 //
 // Exactness. Each residue x < 2^28 is written in balanced base-256 digits,
 //     x = d0 + d1 2^8 + d2 2^16 + d3 2^24,  d0,d1,d2 in [-128, 127], d3 in [0, 16]
-// (byte u of x + 0x808080, minus 128 for u < 3). Every digit is exactly a bf16.
+// (byte u of x + 0x808080, minus 128 for u < 3). Every digit is exactly an fp16.
 // A digit product has |d e| <= 2^14, so a sum of at most 256 of them has
 // magnitude <= 2^22 < 2^24 and is exact in the fp32 accumulator: every partial
 // sum is an integer representable in fp32, so no rounding can occur. Hence
@@ -22,13 +22,13 @@
 // operand stacks the 4 digits of 32 ciphertext rows (M' = 128 rows, ordered
 // m_hi*32 + u*8 + m_lo with m = 8 m_hi + m_lo), the B operand stacks the 4
 // digits of 64 DB columns (N' = 256 rows, ordered n*4 + v); tcgen05.mma
-// .kind::f16 M=128 N=256 K=16, bf16 in, fp32 out. A TMEM lane quarter then
+// .kind::f16 M=128 N=256 K=16, fp16 in, fp32 out. A TMEM lane quarter then
 // holds 8 rows m with all 4 digits u, so the epilogue sums over u with two
 // warp shuffles and over v within the thread.
 //
 // Data movement. The DB is stored once, at upload, as per-slot digit tiles
 // already in the shared-memory image the MMA reads (K-major, 128-byte
-// swizzle): [slot][n-block][k-chunk] x (256 rows x 64 k) bf16. Per batch, an
+// swizzle): [slot][n-block][k-chunk] x (256 rows x 64 k) fp16. Per batch, an
 // ingest kernel turns the p-major ciphertexts into the same image for the A
 // operand ([slot][m-block][k-chunk] x (128 rows x 64 k)), reading 8 slots
 // (one 32-byte sector) per row. The persistent GEMM kernel streams both with
@@ -37,7 +37,7 @@
 // accumulators, so draining overlaps the next group's MMAs) and write the
 // canonical residues in the p-major output layout.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -50,7 +50,7 @@
 namespace gpir {
 namespace {
 
-constexpr int KCHUNK = 64;             // k per pipeline stage (one 128-byte swizzle row of bf16)
+constexpr int KCHUNK = 64;             // k per pipeline stage (one 128-byte swizzle row of fp16)
 constexpr int KGROUP_CHUNKS = 4;       // 4 x 64 = 256 rows per exact fp32 group
 constexpr int MROWS = 32;              // ciphertext rows (m) per tile -> 128 digit rows
 constexpr int NCOLS = 64;              // DB columns per tile -> 256 digit rows
@@ -131,10 +131,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// kind::f16, D = f32, A = B = bf16, both K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::f16, D = f32, A = B = f16 (format 0), both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
@@ -164,13 +164,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // ---- digit helpers -----------------------------------------------------------
 
-// bf16 bit pattern of the balanced digit u (0..3) of x (< 2^28).
-__device__ __forceinline__ uint32_t digit_bf16_bits(uint32_t x, int u) {
+// fp16 bit pattern of the balanced digit u (0..3) of x (< 2^28).
+__device__ __forceinline__ uint32_t digit_f16_bits(uint32_t x, int u) {
   const uint32_t b = x + 0x808080u;
   const uint32_t byte = (b >> (8 * u)) & 0xFFu;
   // 2^23 + byte as an fp32 bit pattern, minus (2^23 + 128) (or 2^23 for the top digit)
   const float f = __int_as_float(0x4B000000 | byte) - (u < 3 ? 8388736.0f : 8388608.0f);
-  return (uint32_t)__float_as_int(f) >> 16;   // exact: |digit| <= 128 fits bf16
+  return (uint32_t)__half_as_ushort(__float2half_rn(f));   // exact: |digit| <= 128 fits fp16
 }
 
 // ---- ingest: p-major ciphertexts -> A-operand digit tiles --------------------
@@ -240,10 +240,10 @@ __global__ void __launch_bounds__(INGEST_THREADS) tc_ingest_kernel(const __grid_
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         uint4 w;
-        w.x = digit_bf16_bits(v[0], u) | (digit_bf16_bits(v[1], u) << 16);
-        w.y = digit_bf16_bits(v[2], u) | (digit_bf16_bits(v[3], u) << 16);
-        w.z = digit_bf16_bits(v[4], u) | (digit_bf16_bits(v[5], u) << 16);
-        w.w = digit_bf16_bits(v[6], u) | (digit_bf16_bits(v[7], u) << 16);
+        w.x = digit_f16_bits(v[0], u) | (digit_f16_bits(v[1], u) << 16);
+        w.y = digit_f16_bits(v[2], u) | (digit_f16_bits(v[3], u) << 16);
+        w.z = digit_f16_bits(v[4], u) | (digit_f16_bits(v[5], u) << 16);
+        w.w = digit_f16_bits(v[6], u) | (digit_f16_bits(v[7], u) << 16);
         const int row = (m_local >> 3) * 32 + u * 8 + (m_local & 7);
         tiles[s * TILE_PAD + row * 8 + (k_oct ^ (row & 7))] = w;
       }
@@ -293,7 +293,7 @@ __global__ void tc_pack_db_kernel(const PackParams p, uint64_t total) {
       const uint32_t k = kc * KCHUNK + k_oct * 8 + kk;
       const uint32_t val =
           (n < p.d1 && k < p.d0) ? p.db[(((uint64_t)k * p.d1 + n) * p.L + l) * p.N + t] : 0u;
-      bits[kk] = digit_bf16_bits(val, (int)v);
+      bits[kk] = digit_f16_bits(val, (int)v);
     }
     uint4 w;
     w.x = bits[0] | (bits[1] << 16);
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
             const uint32_t sb = sa + A_TILE_BYTES;
 #pragma unroll
             for (int k16 = 0; k16 < KCHUNK / 16; ++k16) {
-              mma_bf16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32),
+              mma_f16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32),
                        (kc > c0 || k16 > 0) ? 1u : 0u);
             }
             mma_commit(&empty[st]);      // frees the smem stage once these MMAs have read it
@@ -540,12 +540,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 // launch. Unit ids travel producer -> MMA thread -> epilogue through shared
 // memory with the stage and accumulator barriers. All waits are bounded.
 
-constexpr int FSTAGES = 3;
 constexpr int F_EPI_WARPS = 8;
 constexpr int F_INGEST_WARPS = 8;
 constexpr int FUSED_THREADS = 64 + 32 * F_EPI_WARPS + 32 * F_INGEST_WARPS;   // 576
-constexpr int F_RAW_BYTES = 16 * KCHUNK * 2 * 8 * 4;                         // 64 KB raw box
-constexpr size_t FUSED_SMEM = 1024 + (size_t)FSTAGES * STAGE_BYTES + F_RAW_BYTES + 256;
+// Two shapes of the fused kernel (tile variants): HALF = 32 KB raw boxes of
+// 32 k and 4 operand stages; full = 64 KB boxes of 64 k and 3 stages.
+template <bool HALF>
+struct FusedShape {
+  static constexpr int STAGES = HALF ? 4 : 3;
+  static constexpr int BOX_K = HALF ? KCHUNK / 2 : KCHUNK;         // k per raw box
+  static constexpr int BOXES = KCHUNK / BOX_K;                       // boxes per k-chunk
+  static constexpr int RAW_BYTES = 16 * BOX_K * 2 * 8 * 4;
+  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + RAW_BYTES + 256;
+};
 constexpr uint64_t kNoUnit = ~0ull;
 
 struct FusedParams {
@@ -559,20 +566,20 @@ struct FusedParams {
   unsigned long long *ctr;              // [0] next unit, [1] next ingest task
   unsigned int *err;
   unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
-  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 32 k, 16 clients)
   TcLimb limb[GPIR_MAX_LIMBS];
 };
 
 
-// Two bf16 digits u of x0, x1 (x' = x + 0x808080 precomputed) packed as
-// bf16x2: PRMT puts byte u of x' under the exponent of 2^23, so the fp32 is
-// 2^23 + byte; subtracting 2^23 + 128 (2^23 for the top digit) leaves the
-// digit, exact in bf16.
-__device__ __forceinline__ uint32_t digits2_bf16(uint32_t xp0, uint32_t xp1, int u) {
-  const float off = u < 3 ? 8388736.0f : 8388608.0f;
-  const float f0 = __int_as_float(__byte_perm(xp0, 0x4B000000u, 0x7650u + u)) - off;
-  const float f1 = __int_as_float(__byte_perm(xp1, 0x4B000000u, 0x7650u + u)) - off;
-  __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+// Two fp16 digits u of x0, x1 (x' = x + 0x808080 precomputed) packed as
+// f16x2: PRMT/LOP3 build the halves 0x6400 | byte (= 1024 + byte exactly),
+// one HADD2 subtracts 1024 + 128 (1024 for the top digit) from both.
+__device__ __forceinline__ uint32_t digits2_f16(uint32_t xp0, uint32_t xp1, int u) {
+  const uint32_t t = (__byte_perm(xp0, xp1, (uint32_t)(u | (u << 4) | ((u + 4) << 8) | ((u + 4) << 12))) &
+                      0x00FF00FFu) | 0x64006400u;
+  const __half2 magic = u < 3 ? __half2half2(__ushort_as_half((unsigned short)0xE480))    // -1152
+                              : __half2half2(__ushort_as_half((unsigned short)0xE400));   // -1024
+  __half2 h = __hadd2(*reinterpret_cast<const __half2 *>(&t), magic);
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
@@ -606,8 +613,12 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
 }
 
-template <bool PROF>
+template <bool PROF, bool HALF>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
+  using FS = FusedShape<HALF>;
+  constexpr int FSTAGES = FS::STAGES;
+  constexpr int F_RAW_BYTES = FS::RAW_BYTES;
+  constexpr int F_HALF_K = FS::BOX_K;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *rawbuf = smem + FSTAGES * STAGE_BYTES;
@@ -712,7 +723,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         }
         const uint32_t g = (uint32_t)(E / p.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        if (!(ok = FUSED_TIMED(kPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
+        if (!(ok = FUSED_TIMED(kPWaitReady,
+                               wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch * FS::BOXES))))) break;
         fence_proxy_async_global();
         const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)A_TILE_BYTES;
         const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
@@ -771,7 +783,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
             const uint32_t sb = sa + A_TILE_BYTES;
 #pragma unroll
             for (int k16 = 0; k16 < KCHUNK / 16; ++k16)
-              mma_bf16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32), (kc > c0 || k16 > 0) ? 1u : 0u);
+              mma_f16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32), (kc > c0 || k16 > 0) ? 1u : 0u);
             mma_commit(&empty[st]);
             if (++st == FSTAGES) {
               st = 0;
@@ -874,29 +886,38 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     }
   } else {
     // ---------------- ingest (8 warps, 256 threads) ----------------
-    // Thread (m_local, position cp) reads the 8 slots' residues of row
-    // m_local for k octet k_oct = cp ^ (m_local % 8) and writes, for every
-    // digit u and slot, the 16-byte chunk at position cp of tile row
-    // m_hi*32 + u*8 + m_lo (the swizzled place of that k octet), so each warp
-    // store covers 8 half rows (64 contiguous bytes each) of one tile.
+    // Task = (entry E, k-chunk kc, half h): 32 k of 8 slots x 32 rows, one
+    // 32 KB TMA box. Thread (m_local, j, slot half sh) handles k octet 4h + j
+    // of row m_local for slots 4sh .. 4sh+3; its 16-byte chunk goes to
+    // position cp = (4h + j) ^ (m_local % 8) of tile row m_hi*32 + u*8 + m_lo,
+    // so each warp store covers 8 contiguous 64-byte half rows of one tile.
+    // Every exit decision is uniform over the 256 threads (a value thread 0
+    // publishes before a named barrier, or a barrier AND), so no thread can
+    // leave while the others wait at the next named barrier.
+    // Full boxes (64 k): thread (m_local, j in 0..7) takes k octet j for all 8
+    // slots; half boxes (32 k): thread (m_local, j in 0..3, slot half sh).
+    constexpr int OCT = F_HALF_K / 8;                 // k octets per box
+    constexpr int SLOTS_PER_THREAD = 8 * OCT / 8;     // 8 (full) or 4 (half)
     const int iw = warp - (2 + F_EPI_WARPS);
     const int it = iw * 32 + lane;
-    const int m_hi = iw >> 1, cp = (iw & 1) * 4 + (lane >> 3), m_lo = lane & 7;
+    const int m_hi = iw >> 1, m_lo = lane & 7;
+    const int j = HALF ? (lane >> 3) : ((iw & 1) * 4 + (lane >> 3));
+    const int sh = HALF ? (iw & 1) : 0;
     const int m_local = m_hi * 8 + m_lo;
-    const int cc = m_local >> 1, rp = m_local & 1, k_oct = cp ^ m_lo;
-    // Every exit decision is made uniformly for the 256 ingest threads (a
-    // value thread 0 publishes before a named barrier, or a barrier AND), so
-    // no thread can leave while the others wait at the next named barrier.
+    const int cc = m_local >> 1, rp = m_local & 1;
+    const uint64_t n_half = p.n_tasks * FS::BOXES;
     uint32_t rph = 0;
     bool issued = false;
     for (;;) {
       if (it == 0) {
         const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
-        *task_slot = (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
+        *task_slot = (c < n_half && !*abort_flag) ? c : kNoUnit;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
-      const uint64_t tk = *task_slot;
-      if (tk == kNoUnit) break;
+      const uint64_t c = *task_slot;
+      if (c == kNoUnit) break;
+      const uint64_t tk = c / FS::BOXES;
+      const uint32_t h = (uint32_t)(c % FS::BOXES);
       const uint64_t E = tk / p.kch;
       const uint32_t kc = (uint32_t)(tk % p.kch);
       const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
@@ -906,9 +927,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         // the ring entry's previous occupant must be fully consumed
         if (E < p.R || FUSED_TIMED(kIWaitConsumed, wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe)))) {
           mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
-          tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK), (int)(mb * (MROWS / 2)));
+          tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK + h * F_HALF_K),
+                      (int)(mb * (MROWS / 2)));
           issued = true;
-          *task_slot = tk;
+          *task_slot = c;
         } else {
           *task_slot = kNoUnit;
         }
@@ -927,29 +949,35 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       rph ^= 1u;
       if (it == 0) issued = false;
       const uint64_t tbusy = PROF ? clock64() : 0;
+      const int cp = (int)((h * OCT + j) ^ m_lo);
       const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbuf);
-      uint32_t v[8][8];   // [kk][slot]: residue + 0x808080
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        const int row = (cc * KCHUNK + k_oct * 8 + kk) * 2 + rp;   // 32-byte row: 8 slots
-        const uint4 lo = raw4[row * 2], hi = raw4[row * 2 + 1];
-        v[kk][0] = lo.x + 0x808080u; v[kk][1] = lo.y + 0x808080u; v[kk][2] = lo.z + 0x808080u;
-        v[kk][3] = lo.w + 0x808080u; v[kk][4] = hi.x + 0x808080u; v[kk][5] = hi.y + 0x808080u;
-        v[kk][6] = hi.z + 0x808080u; v[kk][7] = hi.w + 0x808080u;
-      }
       uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
 #pragma unroll
-      for (int sl = 0; sl < 8; ++sl) {
-        if (t0 + sl >= p.N) continue;
-        uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)A_TILE_BYTES) / 16;
+      for (int part = 0; part < SLOTS_PER_THREAD / 4; ++part) {
+        const int s4 = HALF ? sh : part;                // which 4-slot half of the 32-byte row
+        uint32_t v[8][4];   // [kk][slot in half]: residue + 0x808080
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
-          uint4 w4;
-          w4.x = digits2_bf16(v[0][sl], v[1][sl], uu);
-          w4.y = digits2_bf16(v[2][sl], v[3][sl], uu);
-          w4.z = digits2_bf16(v[4][sl], v[5][sl], uu);
-          w4.w = digits2_bf16(v[6][sl], v[7][sl], uu);
-          tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint4 q4 = raw4[((cc * F_HALF_K + j * 8 + kk) * 2 + rp) * 2 + s4];
+          v[kk][0] = q4.x + 0x808080u;
+          v[kk][1] = q4.y + 0x808080u;
+          v[kk][2] = q4.z + 0x808080u;
+          v[kk][3] = q4.w + 0x808080u;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int sl = s4 * 4 + i;
+          if (t0 + sl >= p.N) continue;
+          uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)A_TILE_BYTES) / 16;
+#pragma unroll
+          for (int uu = 0; uu < 4; ++uu) {
+            uint4 w4;
+            w4.x = digits2_f16(v[0][i], v[1][i], uu);
+            w4.y = digits2_f16(v[2][i], v[3][i], uu);
+            w4.z = digits2_f16(v[4][i], v[5][i], uu);
+            w4.w = digits2_f16(v[6][i], v[7][i], uu);
+            tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
+          }
         }
       }
       fence_proxy_async_global();
@@ -1000,7 +1028,7 @@ static TcLimb make_limb(uint32_t q) {
 
 }  // namespace
 
-int rowsel_tc_num_variants() { return 4; }   // 0/2/3: fused, ring 48/24/96 MB; 1: two-pass
+int rowsel_tc_num_variants() { return 5; }   // see rowsel_tc_launch
 int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
 
 int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
@@ -1189,7 +1217,7 @@ bool g_fused_attr_done[64];
 // One RowSel problem through the fused persistent kernel (ingest warps and
 // GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
 int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                    cudaStream_t stream) {
+                    bool half, cudaStream_t stream) {
   if (!db->db_digits) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1198,9 +1226,17 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   {
     std::lock_guard<std::mutex> lk(g_fused_attr_mu);
     if (!g_fused_attr_done[dev]) {
-      e = cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+      e = cudaFuncSetAttribute(tc_fused_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)FusedShape<false>::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+        e = cudaFuncSetAttribute(tc_fused_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FusedShape<false>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fused_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FusedShape<true>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fused_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FusedShape<true>::SMEM);
       if (e != cudaSuccess) return set_cuda_error(e);
       g_fused_attr_done[dev] = true;
     }
@@ -1245,7 +1281,8 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
     const uint64_t dims[5] = {N, L, 2, db->d0, batch};
     const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
                              (uint64_t)db->d0 * 2 * L * N * 4};
-    const uint32_t box[5] = {8, 1, 2, (uint32_t)KCHUNK, (uint32_t)(MROWS / 2)};
+    const uint32_t box_k = half ? (uint32_t)FusedShape<true>::BOX_K : (uint32_t)FusedShape<false>::BOX_K;
+    const uint32_t box[5] = {8, 1, 2, box_k, (uint32_t)(MROWS / 2)};
     rc = encode_tiled_u32(&fp.ct_map, ct, 5, dims, str, box);
     if (rc != GPIR_OK) return rc;
   }
@@ -1255,10 +1292,17 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
   const int grid = sm_count();
   const int tr = trace_begin("tc_fused", stream);
-  if (fp.prof)
-    tc_fused_kernel<true><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
-  else
-    tc_fused_kernel<false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+  if (half) {
+    if (fp.prof)
+      tc_fused_kernel<true, true><<<grid, FUSED_THREADS, FusedShape<true>::SMEM, stream>>>(fp);
+    else
+      tc_fused_kernel<false, true><<<grid, FUSED_THREADS, FusedShape<true>::SMEM, stream>>>(fp);
+  } else {
+    if (fp.prof)
+      tc_fused_kernel<true, false><<<grid, FUSED_THREADS, FusedShape<false>::SMEM, stream>>>(fp);
+    else
+      tc_fused_kernel<false, false><<<grid, FUSED_THREADS, FusedShape<false>::SMEM, stream>>>(fp);
+  }
   trace_end(tr, stream);
   if (fp.prof) trace_counters(fp.prof, kNumFusedCounters, stream);
   e = cudaGetLastError();
@@ -1278,8 +1322,10 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
   }
-  const size_t ring = kRingBytes[variant == 2 ? 1 : variant == 3 ? 2 : 0];
-  return tc_launch_fused(db, batch, ct, out, ring, stream);
+  // 0: 64 KB boxes / 3 stages, ring 48 MB; 2: same, ring 96 MB;
+  // 3: 32 KB boxes / 4 stages, ring 48 MB; 4: same, ring 96 MB; 1: two-pass
+  const size_t ring = kRingBytes[(variant == 2 || variant == 4) ? 2 : 0];
+  return tc_launch_fused(db, batch, ct, out, ring, variant >= 3, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {
