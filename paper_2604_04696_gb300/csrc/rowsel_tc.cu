@@ -121,6 +121,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+__device__ __forceinline__ void st_global_v4_hint(void *dst, const uint4 &v, uint64_t pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
@@ -542,22 +557,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 
 constexpr int F_EPI_WARPS = 8;
 constexpr int F_INGEST_WARPS = 8;
-constexpr int FUSED_THREADS = 64 + 32 * F_EPI_WARPS + 32 * F_INGEST_WARPS;   // 576
-// Two shapes of the fused kernel (tile variants): HALF = 32 KB raw boxes of
-// 32 k and 4 operand stages; full = 64 KB boxes of 64 k and 3 stages.
-template <bool HALF>
-struct FusedShape {
-  static constexpr int STAGES = HALF ? 4 : 3;
-  static constexpr int BOX_K = HALF ? KCHUNK / 2 : KCHUNK;         // k per raw box
-  static constexpr int BOXES = KCHUNK / BOX_K;                       // boxes per k-chunk
-  static constexpr int RAW_BYTES = 16 * BOX_K * 2 * 8 * 4;
-  static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + RAW_BYTES + 256;
-};
+constexpr int F_STORE_WARP = 2 + F_EPI_WARPS + F_INGEST_WARPS;                // output store warp
+constexpr int FUSED_THREADS = 32 * (F_STORE_WARP + 1);                        // 608
+constexpr int FSTAGES = 3;                                     // operand stages (48 KB each)
+constexpr int F_RAW_BYTES = 16 * KCHUNK * 2 * 8 * 4;           // raw box: 16 clients x 2 x 64 k x 8 slots
+constexpr int F_OUT_BYTES = MROWS * NCOLS * 4;                 // one unit's 32 x 64 output block
+constexpr size_t FUSED_SMEM = 1024 + (size_t)FSTAGES * STAGE_BYTES + F_RAW_BYTES + F_OUT_BYTES + 256;
+static_assert(FUSED_SMEM <= 232448, "fused kernel shared memory exceeds 227 KB");
+
 constexpr uint64_t kNoUnit = ~0ull;
+
+// L2 eviction priorities of the fused kernel's streams (tile-variant bits).
+enum FusedHint : uint32_t {
+  kHintCtEvictFirst = 1,     // raw ciphertext TMA boxes: read once
+  kHintDbEvictFirst = 2,     // database digit tiles
+  kHintRingEvictLast = 4,    // digit-ring stores: keep until overwritten
+};
 
 struct FusedParams {
   uint32_t L, N, M, d0, d1, mblk, nblk, kch;
   uint32_t R, gpl;                      // ring entries; 8-slot groups per limb
+  uint32_t hints;                       // FusedHint bits: L2 eviction priorities
+  uint32_t spg;                         // valid slots per group
   uint64_t n_entries, upe, n_units, n_tasks;
   const uint16_t *b_tiles;
   uint32_t *out;
@@ -566,7 +587,7 @@ struct FusedParams {
   unsigned long long *ctr;              // [0] next unit, [1] next ingest task
   unsigned int *err;
   unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
-  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 32 k, 16 clients)
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
   TcLimb limb[GPIR_MAX_LIMBS];
 };
 
@@ -592,6 +613,7 @@ enum FusedCounter {
   kMWaitFull,         // MMA thread waits for operands
   kMWaitAccEmpty,     // MMA thread waits for the epilogue to drain
   kEWaitAccFull,      // epilogue waits for the MMAs
+  kEWaitStage,        // epilogue waits for the store warp to drain out_stage
   kIWaitConsumed,     // ingest waits for a ring entry to be released
   kIWaitBox,          // ingest waits for its TMA box
   kIBusy,             // ingest converting and storing
@@ -613,16 +635,13 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
 }
 
-template <bool PROF, bool HALF>
+template <bool PROF>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
-  using FS = FusedShape<HALF>;
-  constexpr int FSTAGES = FS::STAGES;
-  constexpr int F_RAW_BYTES = FS::RAW_BYTES;
-  constexpr int F_HALF_K = FS::BOX_K;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *rawbuf = smem + FSTAGES * STAGE_BYTES;
-  uint64_t *full = reinterpret_cast<uint64_t *>(rawbuf + F_RAW_BYTES);
+  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbuf + F_RAW_BYTES);   // [32 m][64 n], swizzled
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbuf + F_RAW_BYTES + F_OUT_BYTES);
   uint64_t *empty = full + FSTAGES;
   uint64_t *acc_full = empty + FSTAGES;
   uint64_t *acc_empty = acc_full + 2;
@@ -630,7 +649,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
   uint64_t *stage_unit = raw_bar + 1;                 // [FSTAGES]
   uint64_t *acc_unit = stage_unit + FSTAGES;          // [2]
   uint64_t *task_slot = acc_unit + 2;                 // claimed ingest task
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(task_slot + 1);
+  uint64_t *ostage_full = task_slot + 1;              // out_stage holds a unit's block
+  uint64_t *ostage_empty = ostage_full + 1;           // the store warp has drained it
+  uint64_t *ostage_unit = ostage_empty + 1;           // whose block (or kNoUnit)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ostage_unit + 1);
   volatile uint32_t *abort_flag = tmem_slot + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -644,6 +666,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       mbar_init(&acc_empty[b], F_EPI_WARPS);
     }
     mbar_init(raw_bar, 1);
+    mbar_init(ostage_full, F_EPI_WARPS);
+    mbar_init(ostage_empty, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -690,10 +714,6 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       }
     }
   };
-  auto slot_valid = [&](uint64_t E, uint32_t s) -> bool {
-    const uint32_t g = (uint32_t)(E / p.mblk);
-    return (g % p.gpl) * 8 + s < p.N;
-  };
   uint64_t pc[PROF ? kNumFusedCounters : 1];
 #pragma unroll
   for (int i = 0; i < (PROF ? kNumFusedCounters : 1); ++i) pc[i] = 0;
@@ -712,19 +732,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     if (lane == 0) {
       uint32_t st = 0, ph = 0;
       bool ok = true;
+      const uint64_t pol_first = l2_policy_evict_first();
       for (;;) {
         const uint64_t u = atomicAdd(&p.ctr[0], 1ull);
         if (u >= p.n_units) break;
         const uint64_t E = u / p.upe;
         const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-        if (!slot_valid(E, sl)) {                      // no slot behind this unit (N < 8)
-          atomicAdd(&p.consumed[E % p.R], 1u);
-          continue;
-        }
         const uint32_t g = (uint32_t)(E / p.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
         if (!(ok = FUSED_TIMED(kPWaitReady,
-                               wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch * FS::BOXES))))) break;
+                               wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
         fence_proxy_async_global();
         const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)A_TILE_BYTES;
         const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
@@ -734,7 +751,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
           uint8_t *sa = smem + st * STAGE_BYTES;
           mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
           bulk_g2s(sa, a_src + (uint64_t)kc * A_TILE_BYTES, A_TILE_BYTES, &full[st]);
-          bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st]);
+          if (p.hints & kHintDbEvictFirst)
+            bulk_g2s_hint(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st], pol_first);
+          else
+            bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st]);
           if (++st == FSTAGES) {
             st = 0;
             ph ^= 1u;
@@ -811,7 +831,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     const int m_local = quarter * 8 + m_lo;
     const bool odd = (u & 1) != 0, high = (u & 2) != 0;
     const bool signaller = (warp == 2 && lane == 0);
-    uint32_t buf = 0;
+    const int et = (int)threadIdx.x - 64;   // 0..255 over the epilogue warps
+    // Barrier 2 spans the 256 epilogue threads; every exit decision goes
+    // through a barrier AND, so no thread leaves while others wait there.
+    auto epi_sync = [&]() { asm volatile("bar.sync 2, %0;" ::"n"(32 * F_EPI_WARPS) : "memory"); };
+    auto epi_all = [&](bool v) -> bool {
+      uint32_t r = v ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 2, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(r)
+          : "r"(r), "n"(32 * F_EPI_WARPS)
+          : "memory");
+      return r != 0;
+    };
+    uint32_t buf = 0, oph = 0;
     uint32_t aph[2] = {0, 0};
     uint32_t res[2 * CHUNKS];
 #pragma unroll
@@ -820,16 +854,22 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       bool okw;
       if (warp == 2 && lane == 0) okw = FUSED_TIMED(kEWaitAccFull, wait(&acc_full[buf], aph[buf], kErrMmaWait));
       else okw = wait(&acc_full[buf], aph[buf], kErrMmaWait);
-      if (!okw) break;
+      if (!epi_all(okw)) break;
       tc_fence_after();
       const uint64_t tag = acc_unit[buf];
-      if (tag == kNoUnit) break;
+      if (tag == kNoUnit) {
+        // pass the end of work on to the store warp
+        if (epi_all(wait(ostage_empty, oph ^ 1u, kErrMmaWait))) {
+          if (et == 0) *ostage_unit = kNoUnit;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(ostage_full);
+        }
+        break;
+      }
       const uint64_t un = tag & ~(1ull << 63);
       const bool last = (tag >> 63) != 0;
       const uint64_t E = un / p.upe;
-      const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
-      const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
+      const uint32_t l = (uint32_t)(E / p.mblk) / p.gpl;
       const TcLimb &lm = p.limb[l];
       if (last && signaller) atomicAdd(&p.consumed[E % p.R], 1u);   // its ring tiles are no longer needed
       const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
@@ -869,57 +909,87 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       aph[buf] ^= 1u;
       buf ^= 1u;
       if (last) {
-        const uint32_t m = mb * MROWS + m_local;
-        if (m < p.M) {
-          const uint32_t c = m >> 1, rr = m & 1;
+        // Hand the unit's 32 x 64 block to the store warp through out_stage
+        // (the scattered 4-byte output stores then stay off these warps).
+        const bool oke = (et == 0) ? FUSED_TIMED(kEWaitStage, wait(ostage_empty, oph ^ 1u, kErrMmaWait))
+                                   : wait(ostage_empty, oph ^ 1u, kErrMmaWait);
+        if (!epi_all(oke)) break;
+        const uint32_t swz = (uint32_t)m_lo << 2;   // 16-byte groups swizzled by row: conflict-free
 #pragma unroll
-          for (int j = 0; j < CHUNKS; ++j)
+        for (int j = 0; j < CHUNKS; ++j)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint32_t n = nb * NCOLS + (jbase + j) * 8 + h * 4 + u;
-              if (n < p.d1) p.out[((((uint64_t)c * p.d1 + n) * 2 + rr) * p.L + l) * p.N + t] = res[j * 2 + h];
-            }
-        }
+          for (int h = 0; h < 2; ++h)
+            out_stage[m_local * NCOLS + ((uint32_t)((jbase + j) * 8 + h * 4 + u) ^ swz)] = res[j * 2 + h];
+        if (et == 0) *ostage_unit = un;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ostage_full);
+        oph ^= 1u;
 #pragma unroll
         for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
       }
     }
+  } else if (warp == F_STORE_WARP) {
+    // ---------------- output store warp ----------------
+    // Drains out_stage into the p-major output. out[c][n][r][l][t] has the
+    // slot innermost and a unit owns one slot, so these are 4-byte stores,
+    // one sector each; issuing them here keeps them off the epilogue warps.
+    uint32_t ph = 0;
+    for (;;) {
+      const bool okw = __all_sync(0xffffffffu, wait(ostage_full, ph, kErrMmaWait));
+      if (!okw) break;
+      const uint64_t un = *ostage_unit;
+      if (un == kNoUnit) break;
+      const uint64_t E = un / p.upe;
+      const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
+      const uint32_t mrows = min((uint32_t)MROWS, p.M - mb * MROWS);
+      const uint32_t ncols = min((uint32_t)NCOLS, p.d1 - nb * NCOLS);
+      for (uint32_t m = 0; m < mrows; ++m) {
+        const uint32_t mg = mb * MROWS + m, c = mg >> 1, rr = mg & 1;
+        const uint32_t sw = (m & 7u) << 2;
+        uint32_t *orow = p.out + (((uint64_t)c * p.d1 + nb * NCOLS) * 2 + rr) * p.L * p.N + (uint64_t)l * p.N + t;
+        const uint64_t nstride = (uint64_t)2 * p.L * p.N;
+#pragma unroll
+        for (uint32_t h = 0; h < NCOLS / 32; ++h) {
+          const uint32_t n = h * 32 + lane;
+          if (n < ncols) orow[n * nstride] = out_stage[m * NCOLS + (n ^ sw)];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ostage_empty);
+      ph ^= 1u;
+    }
   } else {
     // ---------------- ingest (8 warps, 256 threads) ----------------
-    // Task = (entry E, k-chunk kc, half h): 32 k of 8 slots x 32 rows, one
-    // 32 KB TMA box. Thread (m_local, j, slot half sh) handles k octet 4h + j
-    // of row m_local for slots 4sh .. 4sh+3; its 16-byte chunk goes to
-    // position cp = (4h + j) ^ (m_local % 8) of tile row m_hi*32 + u*8 + m_lo,
-    // so each warp store covers 8 contiguous 64-byte half rows of one tile.
-    // Every exit decision is uniform over the 256 threads (a value thread 0
-    // publishes before a named barrier, or a barrier AND), so no thread can
-    // leave while the others wait at the next named barrier.
-    // Full boxes (64 k): thread (m_local, j in 0..7) takes k octet j for all 8
-    // slots; half boxes (32 k): thread (m_local, j in 0..3, slot half sh).
-    constexpr int OCT = F_HALF_K / 8;                 // k octets per box
-    constexpr int SLOTS_PER_THREAD = 8 * OCT / 8;     // 8 (full) or 4 (half)
+    // Task = (entry E, k-chunk kc): 64 k of 8 slots x 32 rows, one 64 KB TMA
+    // box. Thread (m_local, j) handles k octet j of row m_local for all 8
+    // slots; its 16-byte chunk goes to position cp = j ^ (m_local % 8) of tile
+    // row m_hi*32 + u*8 + m_lo, so each warp store covers 8 contiguous 64-byte
+    // half rows of one tile. Every exit decision is uniform over the 256
+    // threads (a value thread 0 publishes before a named barrier, or a barrier
+    // AND), so no thread can leave while the others wait at the next named
+    // barrier.
     const int iw = warp - (2 + F_EPI_WARPS);
     const int it = iw * 32 + lane;
     const int m_hi = iw >> 1, m_lo = lane & 7;
-    const int j = HALF ? (lane >> 3) : ((iw & 1) * 4 + (lane >> 3));
-    const int sh = HALF ? (iw & 1) : 0;
+    const int j = (iw & 1) * 4 + (lane >> 3);
     const int m_local = m_hi * 8 + m_lo;
     const int cc = m_local >> 1, rp = m_local & 1;
-    const uint64_t n_half = p.n_tasks * FS::BOXES;
+    const uint64_t pol_first = l2_policy_evict_first(), pol_last = l2_policy_evict_last();
+    const bool ring_last = (p.hints & kHintRingEvictLast) != 0;
     uint32_t rph = 0;
     bool issued = false;
     for (;;) {
       if (it == 0) {
         const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
-        *task_slot = (c < n_half && !*abort_flag) ? c : kNoUnit;
+        *task_slot = (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");
       const uint64_t c = *task_slot;
       if (c == kNoUnit) break;
-      const uint64_t tk = c / FS::BOXES;
-      const uint32_t h = (uint32_t)(c % FS::BOXES);
-      const uint64_t E = tk / p.kch;
-      const uint32_t kc = (uint32_t)(tk % p.kch);
+      const uint64_t E = c / p.kch;
+      const uint32_t kc = (uint32_t)(c % p.kch);
       const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");   // everyone has read task_slot
@@ -927,8 +997,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         // the ring entry's previous occupant must be fully consumed
         if (E < p.R || FUSED_TIMED(kIWaitConsumed, wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe)))) {
           mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
-          tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK + h * F_HALF_K),
-                      (int)(mb * (MROWS / 2)));
+          if (p.hints & kHintCtEvictFirst)
+            tma_load_5d_hint(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK),
+                             (int)(mb * (MROWS / 2)), pol_first);
+          else
+            tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK), (int)(mb * (MROWS / 2)));
           issued = true;
           *task_slot = c;
         } else {
@@ -949,16 +1022,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       rph ^= 1u;
       if (it == 0) issued = false;
       const uint64_t tbusy = PROF ? clock64() : 0;
-      const int cp = (int)((h * OCT + j) ^ m_lo);
+      const int cp = (int)(j ^ m_lo);
       const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbuf);
       uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
 #pragma unroll
-      for (int part = 0; part < SLOTS_PER_THREAD / 4; ++part) {
-        const int s4 = HALF ? sh : part;                // which 4-slot half of the 32-byte row
+      for (int s4 = 0; s4 < 2; ++s4) {                  // which 4-slot half of the 32-byte row
         uint32_t v[8][4];   // [kk][slot in half]: residue + 0x808080
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-          const uint4 q4 = raw4[((cc * F_HALF_K + j * 8 + kk) * 2 + rp) * 2 + s4];
+          const uint4 q4 = raw4[((cc * KCHUNK + j * 8 + kk) * 2 + rp) * 2 + s4];
           v[kk][0] = q4.x + 0x808080u;
           v[kk][1] = q4.y + 0x808080u;
           v[kk][2] = q4.z + 0x808080u;
@@ -976,7 +1048,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
             w4.y = digits2_f16(v[2][i], v[3][i], uu);
             w4.z = digits2_f16(v[4][i], v[5][i], uu);
             w4.w = digits2_f16(v[6][i], v[7][i], uu);
-            tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
+            if (ring_last)
+              st_global_v4_hint(&tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp], w4, pol_last);
+            else
+              tile[(m_hi * 32 + uu * 8 + m_lo) * 8 + cp] = w4;
           }
         }
       }
@@ -1028,7 +1103,6 @@ static TcLimb make_limb(uint32_t q) {
 
 }  // namespace
 
-int rowsel_tc_num_variants() { return 5; }   // see rowsel_tc_launch
 int rowsel_tc_default_variant(uint32_t, uint32_t, uint32_t) { return 0; }
 
 int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
@@ -1207,9 +1281,19 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
   return GPIR_OK;
 }
 
-// Digit-tile ring of the fused kernel, sized against the 129 MB L2 (a tile
-// variant each, picked by the autotuner).
-constexpr size_t kRingBytes[3] = {48ull << 20, 24ull << 20, 96ull << 20};
+// Fused-kernel tile variants: digit-ring size (against the 129 MB L2) and L2
+// eviction hints; the autotuner picks one per shape.
+struct FusedVariant {
+  uint32_t ring_mb;
+  uint32_t hints;
+};
+constexpr FusedVariant kFusedVariants[] = {
+    {48, 0},                                        // 0
+    {0, 0},                                         // 1: two-pass (not fused)
+    {48, kHintCtEvictFirst | kHintRingEvictLast},   // 2
+    {96, 0},                                        // 3
+};
+constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
 std::mutex g_fused_attr_mu;
 bool g_fused_attr_done[64];
@@ -1217,7 +1301,7 @@ bool g_fused_attr_done[64];
 // One RowSel problem through the fused persistent kernel (ingest warps and
 // GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
 int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                    bool half, cudaStream_t stream) {
+                    uint32_t hints, cudaStream_t stream) {
   if (!db->db_digits) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1226,17 +1310,9 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   {
     std::lock_guard<std::mutex> lk(g_fused_attr_mu);
     if (!g_fused_attr_done[dev]) {
-      e = cudaFuncSetAttribute(tc_fused_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)FusedShape<false>::SMEM);
+      e = cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_fused_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)FusedShape<false>::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_fused_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)FusedShape<true>::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_fused_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)FusedShape<true>::SMEM);
+        e = cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
       if (e != cudaSuccess) return set_cuda_error(e);
       g_fused_attr_done[dev] = true;
     }
@@ -1256,7 +1332,8 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.kch = sh.kch;
   fp.gpl = (N + 7) / 8;
   fp.n_entries = (uint64_t)fp.gpl * L * sh.mblk;
-  fp.upe = 8ull * sh.nblk;
+  fp.spg = N < 8 ? N : 8u;                      // N is a power of two >= 4
+  fp.upe = (uint64_t)fp.spg * sh.nblk;          // units per entry: valid slots x n-blocks
   fp.n_units = fp.n_entries * fp.upe;
   fp.n_tasks = fp.n_entries * sh.kch;
   const size_t entry_bytes = (size_t)8 * sh.kch * A_TILE_BYTES;
@@ -1270,39 +1347,33 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   int rc = stream_workspace(stream, ring_bytes + flag_bytes, &ws);
   if (rc != GPIR_OK) return rc;
   fp.ring = ws;
-  fp.ctr = reinterpret_cast<unsigned long long *>(ws + ring_bytes);
-  fp.ready = reinterpret_cast<uint32_t *>(ws + ring_bytes + 16);
+  uint8_t *flags = ws + ring_bytes;
+  fp.ctr = reinterpret_cast<unsigned long long *>(flags);
+  fp.ready = reinterpret_cast<uint32_t *>(flags + 16);
   fp.consumed = fp.ready + R;
   fp.prof = trace_enabled() ? reinterpret_cast<unsigned long long *>(fp.consumed + R) : nullptr;
   if (fp.prof && ((uintptr_t)fp.prof & 7)) fp.prof = reinterpret_cast<unsigned long long *>(((uintptr_t)fp.prof + 7) & ~(uintptr_t)7);
-  e = cudaMemsetAsync(ws + ring_bytes, 0, flag_bytes, stream);
+  e = cudaMemsetAsync(flags, 0, flag_bytes, stream);
   if (e != cudaSuccess) return set_cuda_error(e);
   {
     const uint64_t dims[5] = {N, L, 2, db->d0, batch};
     const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
                              (uint64_t)db->d0 * 2 * L * N * 4};
-    const uint32_t box_k = half ? (uint32_t)FusedShape<true>::BOX_K : (uint32_t)FusedShape<false>::BOX_K;
-    const uint32_t box[5] = {8, 1, 2, box_k, (uint32_t)(MROWS / 2)};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)KCHUNK, (uint32_t)(MROWS / 2)};
     rc = encode_tiled_u32(&fp.ct_map, ct, 5, dims, str, box);
     if (rc != GPIR_OK) return rc;
   }
   fp.b_tiles = db->db_digits;
   fp.out = out;
+  fp.hints = hints;
   fp.err = device_error_word();
   for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
   const int grid = sm_count();
   const int tr = trace_begin("tc_fused", stream);
-  if (half) {
-    if (fp.prof)
-      tc_fused_kernel<true, true><<<grid, FUSED_THREADS, FusedShape<true>::SMEM, stream>>>(fp);
-    else
-      tc_fused_kernel<false, true><<<grid, FUSED_THREADS, FusedShape<true>::SMEM, stream>>>(fp);
-  } else {
-    if (fp.prof)
-      tc_fused_kernel<true, false><<<grid, FUSED_THREADS, FusedShape<false>::SMEM, stream>>>(fp);
-    else
-      tc_fused_kernel<false, false><<<grid, FUSED_THREADS, FusedShape<false>::SMEM, stream>>>(fp);
-  }
+  if (fp.prof)
+    tc_fused_kernel<true><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+  else
+    tc_fused_kernel<false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
   trace_end(tr, stream);
   if (fp.prof) trace_counters(fp.prof, kNumFusedCounters, stream);
   e = cudaGetLastError();
@@ -1310,6 +1381,8 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
 }
 
 }  // namespace
+
+int rowsel_tc_num_variants() { return kNumTcVariants; }
 
 int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
                      cudaStream_t stream) {
@@ -1322,10 +1395,9 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
   }
-  // 0: 64 KB boxes / 3 stages, ring 48 MB; 2: same, ring 96 MB;
-  // 3: 32 KB boxes / 4 stages, ring 48 MB; 4: same, ring 96 MB; 1: two-pass
-  const size_t ring = kRingBytes[(variant == 2 || variant == 4) ? 2 : 0];
-  return tc_launch_fused(db, batch, ct, out, ring, variant >= 3, stream);
+  if (variant < 0 || variant >= kNumTcVariants) return GPIR_EINVAL;
+  const FusedVariant &v = kFusedVariants[variant];
+  return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {

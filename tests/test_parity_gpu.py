@@ -57,6 +57,7 @@ SHAPES = [
     (1, 1, 1, 1, 4, (17,)),                         # degenerate 1 x 1
     (5, 33, 65, 3, 32, (193, 257, 449)),            # three limbs
     (17, 64, 17, 1, 96 * 0 + 64, (268369921,)),     # odd client count
+    (18, 130, 70, 2, 512, synth.PRIMES_28),         # ragged m/n blocks; TC digit and output rings wrap
 ]
 
 
