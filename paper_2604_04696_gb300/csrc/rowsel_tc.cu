@@ -70,6 +70,7 @@ struct TcLimb {
   uint64_t off;       // multiple of q, >= 2^55: makes signed sums non-negative
   int64_t kfix;       // 0x4B400000 * sum_{u,v} c[u+v] (see the epilogue)
   int32_t c[8];       // 2^(8s) mod q, s = 0..6 (c[7] unused)
+  uint64_t off58;     // multiple of q, >= 2^58 (fused kernel: up to 8 groups summed before reducing)
 };
 
 constexpr int MAX_JOBS = 8;            // RowSel problems per launch (inline job table)
@@ -556,6 +557,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 // memory with the stage and accumulator barriers. All waits are bounded.
 
 constexpr int F_EPI_WARPS = 8;
+// Exact fp32 group of the fused kernel: 512 rows, so |D| <= 512 * 2^14 = 2^23,
+// converted exactly with cvt.rni (the magic-number conversion of the two-pass
+// kernel needs |D| < 2^22). Each output sums 16 terms |D| * c < 2^51 per
+// group, so up to 8 groups (< 2^58) are accumulated in 64 bits before one
+// Barrett reduction.
+constexpr int F_KGROUP_CHUNKS = 8;
+constexpr int F_FLUSH_GROUPS = 8;
 constexpr int F_INGEST_WARPS = 8;
 constexpr int F_STORE_WARP = 2 + F_EPI_WARPS + F_INGEST_WARPS;                // output store warp
 constexpr int FUSED_THREADS = 32 * (F_STORE_WARP + 1);                        // 608
@@ -579,6 +587,7 @@ struct FusedParams {
   uint32_t R, gpl;                      // ring entries; 8-slot groups per limb
   uint32_t hints;                       // FusedHint bits: L2 eviction priorities
   uint32_t spg;                         // valid slots per group
+  uint32_t lookahead;                   // ingest runs at most this many entries past the claims (0: ring-bound)
   uint64_t n_entries, upe, n_units, n_tasks;
   const uint16_t *b_tiles;
   uint32_t *out;
@@ -697,6 +706,28 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       }
     }
   };
+  // Bounded wait for the unit claim counter to reach `target`.
+  auto wait_claims = [&](uint64_t target) -> bool {
+    auto seen = [&]() {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&p.ctr[0]) : "memory");
+      return v >= target;
+    };
+    if (seen()) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      __nanosleep(64);
+      if (seen()) return true;
+      if ((n & 15u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, (unsigned int)kErrQueueWait);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
   // Bounded wait for a global counter to reach `target`.
   auto wait_count = [&](const uint32_t *ctr, uint32_t target) -> bool {
     if (ld_acquire(ctr) >= target) return true;
@@ -776,7 +807,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       uint32_t st = 0, ph = 0, buf = 0;
       uint32_t aph[2] = {0, 0};
       bool ok = true;
-      const uint32_t kgroups = (p.kch + KGROUP_CHUNKS - 1) / KGROUP_CHUNKS;
+      const uint32_t kgroups = (p.kch + F_KGROUP_CHUNKS - 1) / F_KGROUP_CHUNKS;
       for (;;) {
         // first stage of the next unit (or the sentinel)
         if (!(ok = FUSED_TIMED(kMWaitFull, wait(&full[st], ph, kErrTmaWait)))) break;
@@ -793,8 +824,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
           if (!(ok = FUSED_TIMED(kMWaitAccEmpty, wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait)))) break;
           tc_fence_after();
           const uint32_t tmem_d = tmem_base + buf * 256;
-          const uint32_t c0 = gi * KGROUP_CHUNKS;
-          const uint32_t c1 = min(p.kch, c0 + KGROUP_CHUNKS);
+          const uint32_t c0 = gi * F_KGROUP_CHUNKS;
+          const uint32_t c1 = min(p.kch, c0 + F_KGROUP_CHUNKS);
           for (uint32_t kc = c0; kc < c1; ++kc) {
             if (!first && !(ok = FUSED_TIMED(kMWaitFull, wait(&full[st], ph, kErrTmaWait)))) break;
             first = false;
@@ -845,11 +876,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
           : "memory");
       return r != 0;
     };
-    uint32_t buf = 0, oph = 0;
+    uint32_t buf = 0, oph = 0, ngroups = 0;
     uint32_t aph[2] = {0, 0};
-    uint32_t res[2 * CHUNKS];
+    uint32_t res[2 * CHUNKS];     // reduced partial results of the current unit
+    int64_t acc64[2 * CHUNKS];    // unreduced group sums since the last reduction
 #pragma unroll
-    for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
+    for (int i = 0; i < 2 * CHUNKS; ++i) {
+      res[i] = 0;
+      acc64[i] = 0;
+    }
     for (;;) {
       bool okw;
       if (warp == 2 && lane == 0) okw = FUSED_TIMED(kEWaitAccFull, wait(&acc_full[buf], aph[buf], kErrMmaWait));
@@ -884,10 +919,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
 #pragma unroll
           for (int ww = 0; ww < 4; ++ww) {
             const int n8 = h * 4 + ww;
-            const int32_t b0 = __float_as_int(__uint_as_float(d[n8 * 4 + 0]) + 12582912.0f);
-            const int32_t b1 = __float_as_int(__uint_as_float(d[n8 * 4 + 1]) + 12582912.0f);
-            const int32_t b2 = __float_as_int(__uint_as_float(d[n8 * 4 + 2]) + 12582912.0f);
-            const int32_t b3 = __float_as_int(__uint_as_float(d[n8 * 4 + 3]) + 12582912.0f);
+            const int32_t b0 = __float2int_rn(__uint_as_float(d[n8 * 4 + 0]));
+            const int32_t b1 = __float2int_rn(__uint_as_float(d[n8 * 4 + 1]));
+            const int32_t b2 = __float2int_rn(__uint_as_float(d[n8 * 4 + 2]));
+            const int32_t b3 = __float2int_rn(__uint_as_float(d[n8 * 4 + 3]));
             P[ww] = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3;
           }
           int64_t k0 = odd ? P[1] : P[0], k1 = odd ? P[3] : P[2];
@@ -897,10 +932,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
           int64_t keep = high ? k1 : k0;
           const int64_t send = high ? k0 : k1;
           keep += __shfl_xor_sync(0xffffffffu, send, 16);
-          const uint32_t rr = reduce64((uint64_t)(keep - lm.kfix + (int64_t)lm.off), lm.q, lm.mu);
-          uint32_t &acc = res[j * 2 + h];
-          acc += rr;
-          acc = acc >= lm.q ? acc - lm.q : acc;
+          acc64[j * 2 + h] += keep;
         }
       }
       tc_fence_before();
@@ -908,6 +940,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
       aph[buf] ^= 1u;
       buf ^= 1u;
+      if (last || ++ngroups == F_FLUSH_GROUPS) {
+        // one Barrett reduction for up to F_FLUSH_GROUPS groups
+#pragma unroll
+        for (int i = 0; i < 2 * CHUNKS; ++i) {
+          const uint32_t rr = reduce64((uint64_t)(acc64[i] + (int64_t)lm.off58), lm.q, lm.mu);
+          const uint32_t a = res[i] + rr;
+          res[i] = a >= lm.q ? a - lm.q : a;
+          acc64[i] = 0;
+        }
+        ngroups = 0;
+      }
       if (last) {
         // Hand the unit's 32 x 64 block to the store warp through out_stage
         // (the scattered 4-byte output stores then stay off these warps).
@@ -994,8 +1037,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory");   // everyone has read task_slot
       if (it == 0) {
-        // the ring entry's previous occupant must be fully consumed
-        if (E < p.R || FUSED_TIMED(kIWaitConsumed, wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe)))) {
+        // the ring entry's previous occupant must be fully consumed, and the
+        // ingest stays within `lookahead` entries of the GEMM units' claims
+        // (so that ring lines are read back while still in L2)
+        const bool near = p.lookahead == 0 || E < p.lookahead ||
+                          FUSED_TIMED(kIWaitConsumed, wait_claims((E - p.lookahead) * p.upe));
+        if (near && (E < p.R || FUSED_TIMED(kIWaitConsumed,
+                                            wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe))))) {
           mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
           if (p.hints & kHintCtEvictFirst)
             tma_load_5d_hint(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(kc * KCHUNK),
@@ -1098,6 +1146,8 @@ static TcLimb make_limb(uint32_t q) {
   for (int u = 0; u < 4; ++u)
     for (int v = 0; v < 4; ++v) csum += t.c[u + v];
   t.kfix = (int64_t)0x4B400000 * csum;
+  const uint64_t two58 = 1ull << 58;
+  t.off58 = ((two58 + q - 1) / q) * (uint64_t)q;
   return t;
 }
 
@@ -1286,12 +1336,17 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
 struct FusedVariant {
   uint32_t ring_mb;
   uint32_t hints;
+  uint32_t lookahead_mb;   // ingest lead over the claim frontier, in ring MB (0: bounded by the ring only)
 };
+constexpr uint32_t kHintRing = kHintCtEvictFirst | kHintRingEvictLast;
 constexpr FusedVariant kFusedVariants[] = {
-    {48, 0},                                        // 0
-    {0, 0},                                         // 1: two-pass (not fused)
-    {48, kHintCtEvictFirst | kHintRingEvictLast},   // 2
-    {96, 0},                                        // 3
+    {48, 0, 0},            // 0
+    {0, 0, 0},             // 1: two-pass (not fused)
+    {48, kHintRing, 0},    // 2
+    {48, 0, 16},           // 3
+    {48, kHintRing, 16},   // 4
+    {48, 0, 20},           // 5
+    {64, 0, 24},           // 6
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
@@ -1301,7 +1356,7 @@ bool g_fused_attr_done[64];
 // One RowSel problem through the fused persistent kernel (ingest warps and
 // GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
 int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                    uint32_t hints, cudaStream_t stream) {
+                    uint32_t hints, uint32_t lookahead_mb, cudaStream_t stream) {
   if (!db->db_digits) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1366,6 +1421,7 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.b_tiles = db->db_digits;
   fp.out = out;
   fp.hints = hints;
+  fp.lookahead = lookahead_mb == 0 ? 0u : (uint32_t)std::max<uint64_t>(2, ((uint64_t)lookahead_mb << 20) / entry_bytes);
   fp.err = device_error_word();
   for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
   const int grid = sm_count();
@@ -1397,7 +1453,7 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
   }
   if (variant < 0 || variant >= kNumTcVariants) return GPIR_EINVAL;
   const FusedVariant &v = kFusedVariants[variant];
-  return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, stream);
+  return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {

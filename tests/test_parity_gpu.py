@@ -100,6 +100,28 @@ def test_worst_case_accumulation(g, path):
 
 
 @pytest.mark.parametrize("path", PATH_LIST)
+@pytest.mark.parametrize("a,b", [(0x7F7F80, 0x7F7F80), (0x7F7F80, 0x7F7F7F), (0x7F7F7F, 0x7F7F7F)])
+def test_extreme_digit_accumulation(g, path, a, b):
+    """Residues whose signed base-256 digits are all at the ends of their range
+    (0x7F7F80 -> -128, -128, -128, 1; 0x7F7F7F -> 127, 127, 127, 0), over
+    D0 = 2048 rows: every exact partial sum of the digit products reaches its
+    bound. The result is D0 * a * b mod q."""
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    _skip_unbuilt(g, PATHS[path])
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 2, 2048, 8, 2, 32
+    ct = np.full((B, D0, 2, L, N), a, dtype=np.uint32)
+    db = np.full((D0, D1, L, N), b, dtype=np.uint32)
+    h = DbHandle(g, db, N, primes, path_mask=PATHS[path])
+    try:
+        got = to_host(h.rowsel(to_dev(ct), B, PATHS[path]))
+    finally:
+        h.close()
+    for l, q in enumerate(primes):
+        assert np.all(got[:, :, :, l] == (D0 * a * b) % q)
+
+
+@pytest.mark.parametrize("path", PATH_LIST)
 def test_one_hot_returns_row(g, path):
     from tests.gpu_util import DbHandle, to_dev, to_host
     _skip_unbuilt(g, PATHS[path])
