@@ -626,6 +626,8 @@ enum FusedCounter {
   kIWaitConsumed,     // ingest waits for a ring entry to be released
   kIWaitBox,          // ingest waits for its TMA box
   kIBusy,             // ingest converting and storing
+  kIWaitSlabs,        // cluster ingest: waiting until the previous slabs have left staging
+  kIPush,             // cluster ingest: issuing the slab copies to the peers
   kCtaCycles,         // whole kernel, per CTA
   kNumFusedCounters
 };
@@ -1129,6 +1131,544 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
 }
 
+// ---- cluster kernel: the 8 CTAs of a cluster share the raw ciphertexts ----
+//
+// A thread-block cluster of 8 CTAs takes one entry E = (8-slot group g,
+// m-block mb) at a time; CTA rank r computes slot r of the group (all n-blocks
+// in turn). The raw residues of the entry arrive p-major, 8 slots per 32-byte
+// row, so each CTA loads only its share of the rows (2 of the 16 clients)
+// with one 8 KB TMA box per k-chunk, splits them into digits for all 8 slots,
+// and stores each slot's digit rows straight into the owning CTA's A stage
+// through distributed shared memory. No digit tile ever leaves the cluster,
+// so the ciphertexts cross HBM once and the L2 sees only raw boxes and
+// database tiles.
+//
+// Per stage st (one k-chunk of one unit (E, nb)) in every CTA:
+//   full_a[st]  8 arrivals: each CTA of the cluster has written its rows
+//   full_b[st]  the CTA's own database tile (bulk copy, 32 KB)
+//   empty[st]   8 arrivals: every CTA's MMAs have read stage st (multicast
+//               commits), so the stage may be refilled everywhere
+// All CTAs walk the same static sequence of stages (entries E = cluster id
+// + i x clusters), so the barrier phases stay aligned across the cluster.
+// All waits are bounded; before exiting, each CTA drains the arrivals that
+// target its own barriers and the cluster synchronizes once, so no CTA
+// leaves while a peer may still write into its shared memory.
+
+constexpr int CL = 8;                                           // CTAs per cluster = slots per group
+constexpr int C_STAGES = 4;                                     // operand stages (48 KB each)
+constexpr int C_SHARE_CLIENTS = 16 / CL;                        // clients of an m-block per CTA
+constexpr int C_RAW_BYTES = C_SHARE_CLIENTS * 2 * KCHUNK * 8 * 4;   // 8 KB share of a raw box
+constexpr int C_SLAB_BYTES = A_TILE_BYTES / CL;                 // one CTA's 16 rows of an A tile (2 KB)
+constexpr int C_STAGING_STRIDE = C_SLAB_BYTES + 16;             // padded: conflict-free staging stores
+constexpr int C_STAGING_BYTES = CL * C_STAGING_STRIDE;
+constexpr size_t CLUSTER_SMEM =
+    1024 + (size_t)C_STAGES * STAGE_BYTES + C_RAW_BYTES + C_STAGING_BYTES + F_OUT_BYTES + 512;
+static_assert(CLUSTER_SMEM <= 232448, "cluster kernel shared memory exceeds 227 KB");
+static_assert(CL == F_INGEST_WARPS, "one ingest warp per k octet and per destination slab");
+
+struct ClusterParams {
+  uint32_t L, N, M, d0, d1, mblk, nblk, kch;
+  uint32_t gpl;
+  uint64_t n_entries;                   // 8-slot groups x m-blocks
+  const uint16_t *b_tiles;
+  uint32_t *out;
+  unsigned int *err;
+  unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 2 clients)
+  TcLimb limb[GPIR_MAX_LIMBS];
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_peer(uint32_t local_saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_saddr), "r"(rank));
+  return r;
+}
+// Arrive on barrier `bar` (same offset) in every CTA of `mask` once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_cluster(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+template <bool PROF>
+__global__ void __launch_bounds__(FUSED_THREADS, 1) tc_cluster_kernel(const __grid_constant__ ClusterParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *rawbuf = smem + C_STAGES * STAGE_BYTES;                                // 8 KB share of a raw box
+  uint8_t *staging = rawbuf + C_RAW_BYTES;                                          // [8 slabs] outgoing rows
+  uint32_t *out_stage = reinterpret_cast<uint32_t *>(staging + C_STAGING_BYTES);    // [32 m][64 n], swizzled
+  uint64_t *full_a = reinterpret_cast<uint64_t *>(staging + C_STAGING_BYTES + F_OUT_BYTES);
+  uint64_t *full_b = full_a + C_STAGES;
+  uint64_t *empty = full_b + C_STAGES;
+  uint64_t *acc_full = empty + C_STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *raw_bar = acc_empty + 2;
+  uint64_t *stage_unit = raw_bar + 1;                 // [C_STAGES]
+  uint64_t *acc_unit = stage_unit + C_STAGES;         // [2]
+  uint64_t *ostage_full = acc_unit + 2;
+  uint64_t *ostage_empty = ostage_full + 1;
+  uint64_t *ostage_unit = ostage_empty + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ostage_unit + 1);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const uint64_t cid = cluster_id_x(), ncl = cluster_count_x();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C_STAGES; ++s) {
+      mbar_init(&full_a[s], 1);      // the owner's expect-tx arrival; the 8 slabs complete the bytes
+      mbar_init(&full_b[s], 1);
+      mbar_init(&empty[s], CL);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 2);
+      mbar_init(&acc_empty[b], F_EPI_WARPS);
+    }
+    mbar_init(raw_bar, 1);
+    mbar_init(ostage_full, F_EPI_WARPS);
+    mbar_init(ostage_empty, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  // every CTA's barriers are initialised before any peer may arrive on them
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  // Bounded wait on one of this CTA's barriers.
+  auto wait_bar = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
+    auto poll = [&]() { return mbar_try_wait(bar, parity); };
+    if (poll()) return true;
+    uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      if (poll()) return true;
+      if ((n & 63u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, code);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  uint64_t pc[PROF ? kNumFusedCounters : 1];
+#pragma unroll
+  for (int i = 0; i < (PROF ? kNumFusedCounters : 1); ++i) pc[i] = 0;
+  const uint64_t kstart = PROF ? clock64() : 0;
+#define CL_TIMED(k, expr)                                  \
+  ([&]() {                                                 \
+    const uint64_t _t0 = PROF ? clock64() : 0;             \
+    const bool _r = (expr);                                \
+    if (PROF) pc[PROF ? (k) : 0] += clock64() - _t0;       \
+    return _r;                                             \
+  }())
+  // entry E -> limb, first slot of its group, m-block
+  auto entry_of = [&](uint64_t E, uint32_t &l, uint32_t &t0, uint32_t &mb) {
+    const uint32_t g = (uint32_t)(E / p.mblk);
+    mb = (uint32_t)(E % p.mblk);
+    l = g / p.gpl;
+    t0 = (g % p.gpl) * 8;
+  };
+
+  if (warp == 0) {
+    // ---------------- producer: this CTA's database tiles ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0;
+      bool ok = true;
+      for (uint64_t E = cid; E < p.n_entries && ok; E += ncl) {
+        uint32_t l, t0, mb;
+        entry_of(E, l, t0, mb);
+        const uint64_t slot = (uint64_t)l * p.N + t0 + rank;
+        for (uint32_t nb = 0; nb < p.nblk && ok; ++nb) {
+          const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
+          for (uint32_t kc = 0; kc < p.kch; ++kc) {
+            if (!(ok = CL_TIMED(kPWaitEmpty, wait_bar(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
+            stage_unit[st] = E * p.nblk + nb;
+            mbar_arrive_expect_tx(&full_a[st], A_TILE_BYTES);   // the 8 CTAs' slabs of this stage
+            uint8_t *sb = smem + st * STAGE_BYTES + A_TILE_BYTES;
+            mbar_arrive_expect_tx(&full_b[st], B_TILE_BYTES);
+            bulk_g2s(sb, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full_b[st]);
+            if (++st == C_STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      }
+      // end of work: one empty stage carrying the sentinel, then drain the
+      // last multicast commits that target this CTA's empty barriers
+      if (ok && wait_bar(&empty[st], ph ^ 1u, kErrTmaWait)) {
+        stage_unit[st] = kNoUnit;
+        mbar_arrive(&full_b[st]);
+      }
+      for (int s2 = 0; s2 < C_STAGES; ++s2) {
+        mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
+        if (++st == C_STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, buf = 0;
+      uint32_t aph[2] = {0, 0};
+      bool ok = true;
+      const uint32_t kgroups = (p.kch + F_KGROUP_CHUNKS - 1) / F_KGROUP_CHUNKS;
+      for (;;) {
+        if (!(ok = CL_TIMED(kMWaitFull, wait_bar(&full_b[st], ph, kErrTmaWait)))) break;
+        const uint64_t u = stage_unit[st];
+        if (u == kNoUnit) {
+          if ((ok = wait_bar(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
+            acc_unit[buf] = kNoUnit;
+            mbar_arrive_cnt(&acc_full[buf], 2);
+          }
+          break;
+        }
+        bool first = true;
+        for (uint32_t gi = 0; gi < kgroups && ok; ++gi) {
+          if (!(ok = CL_TIMED(kMWaitAccEmpty, wait_bar(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait)))) break;
+          tc_fence_after();
+          const uint32_t tmem_d = tmem_base + buf * 256;
+          const uint32_t c0 = gi * F_KGROUP_CHUNKS;
+          const uint32_t c1 = min(p.kch, c0 + F_KGROUP_CHUNKS);
+          for (uint32_t kc = c0; kc < c1; ++kc) {
+            if (!first && !(ok = CL_TIMED(kMWaitFull, wait_bar(&full_b[st], ph, kErrTmaWait)))) break;
+            first = false;
+            if (!(ok = CL_TIMED(kMWaitFull, wait_bar(&full_a[st], ph, kErrTmaWait)))) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sb = sa + A_TILE_BYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < KCHUNK / 16; ++k16)
+              mma_f16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32), (kc > c0 || k16 > 0) ? 1u : 0u);
+            mma_commit_cluster(&empty[st], (uint16_t)((1u << CL) - 1u));
+            if (++st == C_STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          acc_unit[buf] = u | ((gi + 1 == kgroups) ? (1ull << 63) : 0ull);
+          mma_commit(&acc_full[buf]);
+          mbar_arrive(&acc_full[buf]);
+          aph[buf] ^= 1u;
+          buf ^= 1u;
+        }
+        if (!ok) break;
+      }
+      if (!ok)
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&acc_full[b], aph[b], nullptr, 0);
+    }
+  } else if (warp < 2 + F_EPI_WARPS) {
+    // ---------------- epilogue (8 warps) ----------------
+    constexpr int CHUNKS = 8 / (F_EPI_WARPS / 4);
+    const uint32_t quarter = warp & 3;
+    const int jbase = ((warp - 2) >> 2) * CHUNKS;
+    // A rows are ordered m_hi*32 + (m_lo / 4)*16 + 4u + m_lo % 4, so that
+    // each CTA's 16 rows are contiguous: lane = (m_lo / 4)*16 + 4u + m_lo % 4
+    const int u = (lane >> 2) & 3, m_lo = ((lane >> 4) << 2) | (lane & 3);
+    const int m_local = quarter * 8 + m_lo;
+    const bool odd = (u & 1) != 0, high = (u & 2) != 0;
+    const int et = (int)threadIdx.x - 64;
+    auto epi_all = [&](bool v) -> bool {
+      uint32_t r = v ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 2, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(r)
+          : "r"(r), "n"(32 * F_EPI_WARPS)
+          : "memory");
+      return r != 0;
+    };
+    uint32_t buf = 0, oph = 0, ngroups = 0;
+    uint32_t aph[2] = {0, 0};
+    uint32_t res[2 * CHUNKS];
+    int64_t acc64[2 * CHUNKS];
+#pragma unroll
+    for (int i = 0; i < 2 * CHUNKS; ++i) {
+      res[i] = 0;
+      acc64[i] = 0;
+    }
+    for (;;) {
+      bool okw;
+      if (warp == 2 && lane == 0) okw = CL_TIMED(kEWaitAccFull, wait_bar(&acc_full[buf], aph[buf], kErrMmaWait));
+      else okw = wait_bar(&acc_full[buf], aph[buf], kErrMmaWait);
+      if (!epi_all(okw)) break;
+      tc_fence_after();
+      const uint64_t tag = acc_unit[buf];
+      if (tag == kNoUnit) {
+        if (epi_all(wait_bar(ostage_empty, oph ^ 1u, kErrMmaWait))) {
+          if (et == 0) *ostage_unit = kNoUnit;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(ostage_full);
+        }
+        break;
+      }
+      const uint64_t un = tag & ~(1ull << 63);
+      const bool last = (tag >> 63) != 0;
+      const uint64_t E = un / p.nblk;
+      const uint32_t l = (uint32_t)(E / p.mblk) / p.gpl;
+      const TcLimb &lm = p.limb[l];
+      const int32_t c0 = lm.c[u], c1 = lm.c[u + 1], c2 = lm.c[u + 2], c3 = lm.c[u + 3];
+      const uint32_t taddr = tmem_base + ((quarter * 32u) << 16) + buf * 256 + jbase * 32;
+#pragma unroll
+      for (int j = 0; j < CHUNKS; ++j) {
+        uint32_t d[32];
+        tmem_ld32(taddr + j * 32, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t P[4];
+#pragma unroll
+          for (int ww = 0; ww < 4; ++ww) {
+            const int n8 = h * 4 + ww;
+            const int32_t b0 = __float2int_rn(__uint_as_float(d[n8 * 4 + 0]));
+            const int32_t b1 = __float2int_rn(__uint_as_float(d[n8 * 4 + 1]));
+            const int32_t b2 = __float2int_rn(__uint_as_float(d[n8 * 4 + 2]));
+            const int32_t b3 = __float2int_rn(__uint_as_float(d[n8 * 4 + 3]));
+            P[ww] = (int64_t)b0 * c0 + (int64_t)b1 * c1 + (int64_t)b2 * c2 + (int64_t)b3 * c3;
+          }
+          int64_t k0 = odd ? P[1] : P[0], k1 = odd ? P[3] : P[2];
+          const int64_t s0 = odd ? P[0] : P[1], s1 = odd ? P[2] : P[3];
+          k0 += __shfl_xor_sync(0xffffffffu, s0, 4);    // partner lane: u ^ 1
+          k1 += __shfl_xor_sync(0xffffffffu, s1, 4);
+          int64_t keep = high ? k1 : k0;
+          const int64_t send = high ? k0 : k1;
+          keep += __shfl_xor_sync(0xffffffffu, send, 8);  // partner lane: u ^ 2
+          acc64[j * 2 + h] += keep;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      aph[buf] ^= 1u;
+      buf ^= 1u;
+      if (last || ++ngroups == F_FLUSH_GROUPS) {
+#pragma unroll
+        for (int i = 0; i < 2 * CHUNKS; ++i) {
+          const uint32_t rr = reduce64((uint64_t)(acc64[i] + (int64_t)lm.off58), lm.q, lm.mu);
+          const uint32_t a = res[i] + rr;
+          res[i] = a >= lm.q ? a - lm.q : a;
+          acc64[i] = 0;
+        }
+        ngroups = 0;
+      }
+      if (last) {
+        const bool oke = (et == 0) ? CL_TIMED(kEWaitStage, wait_bar(ostage_empty, oph ^ 1u, kErrMmaWait))
+                                   : wait_bar(ostage_empty, oph ^ 1u, kErrMmaWait);
+        if (!epi_all(oke)) break;
+        const uint32_t swz = (uint32_t)m_lo << 2;
+#pragma unroll
+        for (int j = 0; j < CHUNKS; ++j)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            out_stage[m_local * NCOLS + ((uint32_t)((jbase + j) * 8 + h * 4 + u) ^ swz)] = res[j * 2 + h];
+        if (et == 0) *ostage_unit = un;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ostage_full);
+        oph ^= 1u;
+#pragma unroll
+        for (int i = 0; i < 2 * CHUNKS; ++i) res[i] = 0;
+      }
+    }
+  } else if (warp == F_STORE_WARP) {
+    // ---------------- output store warp (slot `rank` of the group) ----------------
+    uint32_t ph = 0;
+    for (;;) {
+      const bool okw = __all_sync(0xffffffffu, wait_bar(ostage_full, ph, kErrMmaWait));
+      if (!okw) break;
+      const uint64_t un = *ostage_unit;
+      if (un == kNoUnit) break;
+      const uint64_t E = un / p.nblk;
+      const uint32_t nb = (uint32_t)(un % p.nblk);
+      uint32_t l, t0, mb;
+      entry_of(E, l, t0, mb);
+      const uint32_t t = t0 + rank;
+      const uint32_t mrows = min((uint32_t)MROWS, p.M - mb * MROWS);
+      const uint32_t ncols = min((uint32_t)NCOLS, p.d1 - nb * NCOLS);
+      for (uint32_t m = 0; m < mrows; ++m) {
+        const uint32_t mg = mb * MROWS + m, c = mg >> 1, rr = mg & 1;
+        const uint32_t sw = (m & 7u) << 2;
+        uint32_t *orow = p.out + (((uint64_t)c * p.d1 + nb * NCOLS) * 2 + rr) * p.L * p.N + (uint64_t)l * p.N + t;
+        const uint64_t nstride = (uint64_t)2 * p.L * p.N;
+#pragma unroll
+        for (uint32_t h = 0; h < NCOLS / 32; ++h) {
+          const uint32_t n = h * 32 + lane;
+          if (n < ncols) orow[n * nstride] = out_stage[m * NCOLS + (n ^ sw)];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ostage_empty);
+      ph ^= 1u;
+    }
+  } else {
+    // ---------------- ingest (8 warps, 256 threads) ----------------
+    // This CTA's share of entry E is clients 2r, 2r+1 of the m-block: rows
+    // m = 4r .. 4r+3 (m = 2 client + polynomial), which in every slot's A
+    // tile are the 16 contiguous rows 16r .. 16r+15 (row = 16r + 4u + mm).
+    // Warp j takes k octet j; lane (mm, s) takes row 4r + mm of slot s and
+    // writes its four 16-byte digit chunks (u = 0..3) into the staging slab
+    // of destination CTA s, already in the SW128 position (j ^ (row % 8)).
+    // Thread 0 then pushes the 8 slabs (2 KB each) to their CTAs with bulk
+    // copies that complete on the owners' full_a barriers. Exit decisions go
+    // through a barrier AND.
+    const int it = (warp - (2 + F_EPI_WARPS)) * 32 + lane;     // 0..255 (ingest warps 10..17)
+    const int j = warp - (2 + F_EPI_WARPS);                     // k octet
+    const uint32_t s = (uint32_t)(lane & 7);                    // destination slot = CTA rank
+    const int mm = lane >> 3;                                   // row of the share
+    const int c2 = mm >> 1, comp = mm & 1;
+    auto iall = [&](bool v) -> bool {
+      uint32_t r = v ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(r)
+          : "r"(r), "n"(32 * F_INGEST_WARPS)
+          : "memory");
+      return r != 0;
+    };
+    auto isync = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(32 * F_INGEST_WARPS) : "memory"); };
+    const uint32_t smem_base = smem_u32(smem);
+    const uint32_t my_full_a = smem_u32(full_a);
+    const uint32_t staging_s = smem_u32(staging);
+    // staging byte offsets of this thread's four chunks
+    uint32_t soff[4];
+#pragma unroll
+    for (int uu = 0; uu < 4; ++uu)
+      soff[uu] = s * C_STAGING_STRIDE + (uint32_t)((uu * 4 + mm) * 128 + ((j ^ ((uu & 1) * 4 + mm)) * 16));
+    uint64_t E = cid;
+    uint32_t nb = 0, kc = 0;
+    auto issue_box = [&](uint64_t e, uint32_t k) {
+      uint32_t l, t0, mb;
+      entry_of(e, l, t0, mb);
+      mbar_arrive_expect_tx(raw_bar, C_RAW_BYTES);
+      tma_load_5d(rawbuf, &p.ct_map, raw_bar, (int)t0, (int)l, 0, (int)(k * KCHUNK),
+                  (int)(mb * 16 + rank * C_SHARE_CLIENTS));
+    };
+    uint32_t st = 0, ph = 0, rph = 0;
+    bool issued = false, copies = false;
+    if (it == 0 && E < p.n_entries) {
+      issue_box(E, 0);
+      issued = true;
+    }
+    while (E < p.n_entries) {
+      uint64_t En = E;
+      uint32_t nbn = nb, kcn = kc + 1;
+      if (kcn == p.kch) {
+        kcn = 0;
+        if (++nbn == p.nblk) {
+          nbn = 0;
+          En += ncl;
+        }
+      }
+      bool ok = (it == 0) ? CL_TIMED(kIWaitBox, wait_bar(raw_bar, rph, kErrTmaWait))
+                          : wait_bar(raw_bar, rph, kErrTmaWait);
+      ok = ok && ((it == 0) ? CL_TIMED(kIWaitConsumed, wait_bar(&empty[st], ph ^ 1u, kErrTmaWait))
+                            : wait_bar(&empty[st], ph ^ 1u, kErrTmaWait));
+      if (!iall(ok)) break;
+      rph ^= 1u;
+      if (it == 0) issued = false;
+      const uint64_t tbusy = PROF ? clock64() : 0;
+      // raw box layout: [client c2][k][poly][slot], 4 bytes each
+      const uint32_t *raw = reinterpret_cast<const uint32_t *>(rawbuf);
+      uint32_t v[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) v[kk] = raw[((c2 * KCHUNK + j * 8 + kk) * 2 + comp) * 8 + s] + 0x808080u;
+      isync();   // the raw box is read: prefetch the next one; the previous slabs must have left staging
+      if (it == 0 && En < p.n_entries) {
+        issue_box(En, kcn);
+        issued = true;
+      }
+      if (lane == 0 && copies) {
+        const uint64_t tw = PROF ? clock64() : 0;
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // this warp's slab copy
+        if (PROF && j == 0) pc[PROF ? kIWaitSlabs : 0] += clock64() - tw;
+      }
+      isync();
+#pragma unroll
+      for (int uu = 0; uu < 4; ++uu) {
+        uint4 w4;
+        w4.x = digits2_f16(v[0], v[1], uu);
+        w4.y = digits2_f16(v[2], v[3], uu);
+        w4.z = digits2_f16(v[4], v[5], uu);
+        w4.w = digits2_f16(v[6], v[7], uu);
+        *reinterpret_cast<uint4 *>(staging + soff[uu]) = w4;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the bulk copies read staging
+      isync();
+      if (lane == 0) {
+        // warp j pushes slab j (this CTA's rows of stage st) to CTA j
+        const uint64_t tpush = PROF ? clock64() : 0;
+        const uint32_t d = (uint32_t)j;
+        const uint32_t dst_local = smem_base + st * STAGE_BYTES + rank * C_SLAB_BYTES;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                map_peer(dst_local, d)),
+            "r"(staging_s + d * C_STAGING_STRIDE), "n"(C_SLAB_BYTES), "r"(map_peer(my_full_a + st * 8, d))
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        copies = true;
+        if (PROF && j == 0) pc[PROF ? kIPush : 0] += clock64() - tpush;
+      }
+      if (PROF) pc[PROF ? kIBusy : 0] += clock64() - tbusy;
+      if (++st == C_STAGES) {
+        st = 0;
+        ph ^= 1u;
+      }
+      E = En;
+      nb = nbn;
+      kc = kcn;
+    }
+    if (it == 0 && issued) mbar_wait_bounded(raw_bar, rph, nullptr, 0);   // let a late box land
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // this warp's slabs have landed
+  }
+#undef CL_TIMED
+  if (PROF) {
+    const bool counter = (lane == 0) && (warp <= 2 || warp == 2 + F_EPI_WARPS);
+    if (counter)
+      for (int i = 0; i < (PROF ? kNumFusedCounters : 1) - 1; ++i)
+        if (pc[i]) atomicAdd(&p.prof[i], pc[i]);
+    if (threadIdx.x == 0) atomicAdd(&p.prof[kCtaCycles], clock64() - kstart);
+  }
+  tc_fence_before();
+  __syncthreads();
+  // no peer may still be writing into this CTA's shared memory or arriving
+  // on its barriers once every CTA has passed this point
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+}
+
 static TcLimb make_limb(uint32_t q) {
   TcLimb t;
   t.q = q;
@@ -1333,20 +1873,22 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
 
 // Fused-kernel tile variants: digit-ring size (against the 129 MB L2) and L2
 // eviction hints; the autotuner picks one per shape.
+enum TcKernelKind : uint32_t { kKindFused = 0, kKindTwoPass = 1, kKindCluster = 2 };
 struct FusedVariant {
+  uint32_t kind;           // TcKernelKind
   uint32_t ring_mb;
   uint32_t hints;
   uint32_t lookahead_mb;   // ingest lead over the claim frontier, in ring MB (0: bounded by the ring only)
 };
 constexpr uint32_t kHintRing = kHintCtEvictFirst | kHintRingEvictLast;
 constexpr FusedVariant kFusedVariants[] = {
-    {48, 0, 0},            // 0
-    {0, 0, 0},             // 1: two-pass (not fused)
-    {48, kHintRing, 0},    // 2
-    {48, 0, 16},           // 3
-    {48, kHintRing, 16},   // 4
-    {48, 0, 20},           // 5
-    {64, 0, 24},           // 6
+    {kKindFused, 48, 0, 16},            // 0
+    {kKindTwoPass, 0, 0, 0},            // 1: two-pass (ingest to HBM, then GEMM)
+    {kKindFused, 48, kHintRing, 0},     // 2
+    {kKindFused, 48, 0, 0},             // 3
+    {kKindFused, 48, kHintRing, 16},    // 4
+    {kKindFused, 40, kHintRing, 16},    // 5
+    {kKindCluster, 0, 0, 0},            // 6: 8-CTA clusters sharing raw boxes over DSMEM
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
@@ -1436,13 +1978,126 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
 
+
+std::mutex g_cluster_mu;
+int g_cluster_count[64];   // active 8-CTA clusters per device (0: not queried yet, -1: none fit)
+
+// One RowSel problem through the cluster kernel. GPIR_ENOTSUP when the ring
+// has fewer than 8 slots or no 8-CTA cluster can be resident.
+int tc_launch_cluster(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, cudaStream_t stream) {
+  if (!db->db_digits) return GPIR_ENOTSUP;
+  const gpir_params &prm = db->params;
+  const uint32_t L = prm.num_limbs, N = prm.n;
+  if (N < (uint32_t)CL) return GPIR_ENOTSUP;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  const int grid_max = sm_count();
+  {
+    std::lock_guard<std::mutex> lk(g_cluster_mu);
+    if (g_cluster_count[dev] == 0) {
+      e = cudaFuncSetAttribute(tc_cluster_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CLUSTER_SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_cluster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CLUSTER_SMEM);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      cudaLaunchConfig_t cfg;
+      memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = dim3((unsigned)(grid_max / CL * CL));
+      cfg.blockDim = dim3(FUSED_THREADS);
+      cfg.dynamicSmemBytes = CLUSTER_SMEM;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, tc_cluster_kernel<false>, &cfg);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+      g_cluster_count[dev] = n > 0 ? n : -1;
+    }
+  }
+  if (g_cluster_count[dev] < 0) return GPIR_ENOTSUP;
+  const TcShape sh = tc_shape(db, batch);
+  ClusterParams cp;
+  memset(&cp, 0, sizeof(cp));
+  cp.L = L;
+  cp.N = N;
+  cp.M = sh.M;
+  cp.d0 = db->d0;
+  cp.d1 = db->d1;
+  cp.mblk = sh.mblk;
+  cp.nblk = sh.nblk;
+  cp.kch = sh.kch;
+  cp.gpl = N / 8;
+  cp.n_entries = (uint64_t)cp.gpl * L * sh.mblk;
+  cp.b_tiles = db->db_digits;
+  cp.out = out;
+  cp.err = device_error_word();
+  for (uint32_t l = 0; l < L; ++l) cp.limb[l] = make_limb(prm.primes[l]);
+  {
+    const uint64_t dims[5] = {N, L, 2, db->d0, batch};
+    const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
+                             (uint64_t)db->d0 * 2 * L * N * 4};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)KCHUNK, (uint32_t)C_SHARE_CLIENTS};
+    const int rc = encode_tiled_u32(&cp.ct_map, ct, 5, dims, str, box);
+    if (rc != GPIR_OK) return rc;
+  }
+  uint8_t *ws = nullptr;
+  if (trace_enabled()) {
+    const int rc = stream_workspace(stream, 8 * kNumFusedCounters, &ws);
+    if (rc != GPIR_OK) return rc;
+    e = cudaMemsetAsync(ws, 0, 8 * kNumFusedCounters, stream);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    cp.prof = reinterpret_cast<unsigned long long *>(ws);
+  }
+  uint64_t clusters = (uint64_t)g_cluster_count[dev];
+  if (clusters > cp.n_entries) clusters = cp.n_entries;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)(clusters * CL));
+  cfg.blockDim = dim3(FUSED_THREADS);
+  cfg.dynamicSmemBytes = CLUSTER_SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int tr = trace_begin("tc_cluster", stream);
+  if (cp.prof)
+    e = cudaLaunchKernelEx(&cfg, tc_cluster_kernel<true>, cp);
+  else
+    e = cudaLaunchKernelEx(&cfg, tc_cluster_kernel<false>, cp);
+  trace_end(tr, stream);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (cp.prof) trace_counters(cp.prof, kNumFusedCounters, stream);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
 }  // namespace
 
 int rowsel_tc_num_variants() { return kNumTcVariants; }
 
 int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, int variant,
                      cudaStream_t stream) {
-  if (variant == 1) {
+  if (variant < 0 || variant >= kNumTcVariants) return GPIR_EINVAL;
+  const FusedVariant &v = kFusedVariants[variant];
+  if (v.kind == kKindCluster) {
+    const int rc = tc_launch_cluster(db, batch, ct, out, stream);
+    if (rc != GPIR_ENOTSUP) return rc;
+    return tc_launch_fused(db, batch, ct, out, (size_t)48 << 20, 0, 16, stream);   // N < 8 or no cluster fits
+  }
+  if (v.kind == kKindTwoPass) {
     gpir_job_t job;
     job.db = db;
     job.batch = batch;
@@ -1451,8 +2106,6 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
   }
-  if (variant < 0 || variant >= kNumTcVariants) return GPIR_EINVAL;
-  const FusedVariant &v = kFusedVariants[variant];
   return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, stream);
 }
 

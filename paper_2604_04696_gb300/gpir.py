@@ -250,7 +250,7 @@ def gpir_trace_read(max_records=4096):
 
 FUSED_COUNTERS = ["producer_wait_ready", "producer_wait_empty", "mma_wait_full", "mma_wait_acc_empty",
                   "epilogue_wait_acc_full", "epilogue_wait_stage", "ingest_wait_consumed", "ingest_wait_box",
-                  "ingest_busy", "cta_cycles"]
+                  "ingest_busy", "ingest_wait_slabs", "ingest_push", "cta_cycles"]
 
 
 def gpir_trace_counters():
