@@ -201,7 +201,7 @@ def kernel_roofline(name, w, ms, peaks, workload):
     alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     s = ms / 1e3
-    path_id = {"rowsel_cc": 1, "rowsel_imma": 2, "tc_gemm": 4, "tc_ingest": 4, "tc_fused": 4}[name]
+    path_id = {"rowsel_cc": 1, "rowsel_imma": 2, "tc_gemm": 4, "tc_ingest": 4, "tc_fused": 4, "tc_cluster": 4}[name]
     traffic = recorded_traffic(name, workload, w["B"], path_id)
     if name == "tc_ingest":
         b = sizes.query_ct_bytes(w["B"], w["D0"], w["N"], w["L"])
