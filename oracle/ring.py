@@ -9,6 +9,8 @@ is what makes RowSel point-wise.
 Everything is O(N^2) by definition, with no butterflies: slow and easy to read.
 """
 
+import functools
+
 import numpy as np
 
 
@@ -91,27 +93,28 @@ def _modmatvec(w: np.ndarray, a: np.ndarray, q: int) -> np.ndarray:
     return out
 
 
+@functools.lru_cache(maxsize=8)
+def _ntt_matrix(q: int, psi: int, n: int, inverse: bool) -> np.ndarray:
+    """W[s][j] = psi^((2s+1) j) (forward) or W[j][s] = psi^-((2s+1) j) (inverse), mod q.
+    Memoised: the definition's matrix does not depend on the data."""
+    base = pow(psi, q - 2, q) if inverse else psi
+    pw = _power_table(base, 2 * n, q)
+    r = np.arange(n, dtype=np.int64)[:, None]
+    c = np.arange(n, dtype=np.int64)[None, :]
+    return pw[((2 * c + 1) * r) % (2 * n)] if inverse else pw[((2 * r + 1) * c) % (2 * n)]
+
+
 def ntt_negacyclic(a, q: int, psi: int) -> np.ndarray:
     """Natural-order negacyclic NTT by definition: A_s = sum_j a_j psi^((2s+1) j) mod q."""
     a = np.asarray(a, dtype=np.uint64)
-    n = a.shape[0]
-    pw = _power_table(psi, 2 * n, q)
-    s = np.arange(n, dtype=np.int64)[:, None]
-    j = np.arange(n, dtype=np.int64)[None, :]
-    w = pw[((2 * s + 1) * j) % (2 * n)]
-    return _modmatvec(w, a, q)
+    return _modmatvec(_ntt_matrix(q, psi, a.shape[0], False), a, q)
 
 
 def intt_negacyclic(A, q: int, psi: int) -> np.ndarray:
     """Inverse of ntt_negacyclic: a_j = n^-1 sum_s A_s psi^-((2s+1) j) mod q."""
     A = np.asarray(A, dtype=np.uint64)
     n = A.shape[0]
-    psi_inv = pow(psi, q - 2, q)
-    pw = _power_table(psi_inv, 2 * n, q)
-    j = np.arange(n, dtype=np.int64)[:, None]
-    s = np.arange(n, dtype=np.int64)[None, :]
-    w = pw[((2 * s + 1) * j) % (2 * n)]
-    a = _modmatvec(w, A, q)
+    a = _modmatvec(_ntt_matrix(q, psi, n, True), A, q)
     n_inv = pow(n, q - 2, q)
     return (a * np.uint64(n_inv)) % np.uint64(q)
 

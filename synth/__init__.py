@@ -1,6 +1,7 @@
-"""Seeded synthetic inputs for RowSel, shared by the oracle tests and the GPU path.
+"""Seeded synthetic inputs for RowSel and ColTor, shared by the oracle tests and the GPU path.
 
-This module holds no RowSel arithmetic. It draws uniform residues from a
+This module holds no RowSel or ColTor arithmetic (the toy RLWE / RGSW
+encryptions are client-side inputs). It draws uniform residues from a
 counter-based generator so any element can be produced independently and the
 same stream can be reproduced on the host and on the device.
 
@@ -16,7 +17,8 @@ A residue mod q is value(i) mod q (bias below 2^-36 for q < 2^28).
 from .gen import (GAMMA, mix64, stream_key, uniform_u64, uniform_residues, residues_at,
                   uniform_u64_at, ct_slots, db_slots,
                   ct_tensor, db_tensor, TAG_DB, TAG_CT, TAG_SECRET, TAG_MASK,
-                  toy_rlwe_selection, config_shapes, CONFIGS, PRIMES_28)
+                  toy_rlwe_selection, config_shapes, CONFIGS, PRIMES_28,
+                  TAG_RGSW, TAG_COLTOR, TAG_RECORD, toy_rgsw, toy_coltor_inputs)
 
 __all__ = ["GAMMA", "mix64", "stream_key", "uniform_u64", "uniform_residues", "residues_at",
            "uniform_u64_at", "ct_slots", "db_slots",

@@ -12,6 +12,9 @@ TAG_DB = 1        # database residues
 TAG_CT = 2        # selection-ciphertext residues
 TAG_SECRET = 3    # toy RLWE secret
 TAG_MASK = 4      # toy RLWE uniform "a" polynomials
+TAG_RGSW = 5      # toy RGSW uniform "a" polynomials (ColTor inputs)
+TAG_COLTOR = 6    # toy RLWE uniform "a" polynomials of ColTor's input ciphertexts
+TAG_RECORD = 7    # records (plaintext polynomials) those ciphertexts encrypt
 
 # The two largest primes below 2^28 that are 1 mod 8192 (so NTT-friendly for
 # every N <= 4096): 0xFFF0001 and 0xFFEE001.
@@ -92,6 +95,48 @@ def toy_rlwe_selection(seed: int, D0: int, L: int, N: int, primes, istar: int):
         ct[:, 0, l, :] = a[:, l, :].astype(np.uint32)
         ct[:, 1, l, :] = b.astype(np.uint32)
     return ct, s.astype(np.uint32)
+
+
+def toy_rgsw(seed: int, stage: int, m: int, s, L: int, N: int, primes, ell: int, log_base: int = 22):
+    """Noiseless toy RGSW encryption of the bit m under secret s (NTT domain), for
+    ColTor inputs: rows i < ell are (a_i + m g_i, a_i (.) s), rows ell + i are
+    (a'_i, a'_i (.) s + m g_i), with g_i = 2^(log_base i) mod q_l a constant
+    polynomial (its NTT is the constant vector). Returns [2 ell][2][L][N] uint32.
+    This is key material the client makes, not part of ColTor.
+    """
+    a = uniform_residues(seed, TAG_RGSW, (stage + 1, 2 * ell, L, N), primes, limb_axis=2)[stage].astype(np.uint64)
+    s = np.asarray(s, dtype=np.uint64)
+    out = np.empty((2 * ell, 2, L, N), dtype=np.uint32)
+    for l in range(L):
+        q = np.uint64(primes[l])
+        for row in range(2 * ell):
+            i = row % ell
+            g = np.uint64(pow(2, log_base * i, int(primes[l])) * int(m) % int(primes[l]))
+            ar = a[row, l]
+            c0 = (ar + g) % q if row < ell else ar
+            c1 = (ar * s[l]) % q if row < ell else ((ar * s[l]) % q + g) % q
+            out[row, 0, l] = c0.astype(np.uint32)
+            out[row, 1, l] = c1.astype(np.uint32)
+    return out
+
+
+def toy_coltor_inputs(seed: int, D1: int, L: int, N: int, primes, jstar: int, ell: int, log_base: int = 22):
+    """ColTor inputs for one client with a known answer: D1 noiseless toy RLWE
+    ciphertexts ct_j = (a_j, a_j (.) s + R_j) of random records R_j (NTT domain),
+    and one toy RGSW encryption of each bit of jstar (least significant first).
+    Returns (ct [D1][2][L][N], rgsw [log2 D1][2 ell][2][L][N], s [L][N], R [D1][L][N])."""
+    stages = max(0, int(D1).bit_length() - 1)
+    s = uniform_residues(seed, TAG_SECRET, (L, N), primes, limb_axis=0)
+    a = uniform_residues(seed, TAG_COLTOR, (D1, L, N), primes, limb_axis=1).astype(np.uint64)
+    rec = uniform_residues(seed, TAG_RECORD, (D1, L, N), primes, limb_axis=1)
+    ct = np.empty((D1, 2, L, N), dtype=np.uint32)
+    for l in range(L):
+        q = np.uint64(primes[l])
+        ct[:, 0, l] = a[:, l].astype(np.uint32)
+        ct[:, 1, l] = ((a[:, l] * s[l].astype(np.uint64)) % q + rec[:, l].astype(np.uint64)) % q
+    rgsw = np.stack([toy_rgsw(seed, st, (jstar >> st) & 1, s, L, N, primes, ell, log_base)
+                     for st in range(stages)]) if stages else np.zeros((0, 2 * ell, 2, L, N), np.uint32)
+    return ct, rgsw, s, rec
 
 
 # Workloads of the GPIR RowSel study on one GB300 (synthetic, uniform residues).
