@@ -222,14 +222,44 @@ typedef struct gpir_trace_record {
 } gpir_trace_record_t;
 int gpir_trace_enable(int on);
 int gpir_trace_read(gpir_trace_record_t *out, uint32_t max_records, uint32_t *count);
-/* Wait-cycle counters of the last fused tensor-core launch made while tracing
- * was on (SM clock cycles summed over CTAs, one counting thread per role):
- * [0] producer waiting for ingested tiles, [1] producer waiting for a free
- * stage, [2] MMA waiting for operands, [3] MMA waiting for the epilogue,
- * [4] epilogue waiting for MMAs, [5] ingest waiting for a ring entry,
- * [6] ingest waiting for its TMA box, [7] ingest converting, [8] kernel
- * cycles per CTA. Tracing makes that launch synchronous. */
+/* Wait-cycle counters of the last fused or cluster tensor-core launch made
+ * while tracing was on (SM clock cycles summed over CTAs, one counting thread
+ * per role): [0] producer waiting for ingested tiles, [1] producer waiting for
+ * a free stage, [2] MMA waiting for operands, [3] MMA waiting for the
+ * epilogue, [4] epilogue waiting for MMAs, [5] epilogue waiting for the store
+ * warp, [6] ingest waiting for a ring entry (cluster kernel: for a free stage),
+ * [7] ingest waiting for its TMA box, [8] ingest converting, [9] cluster
+ * ingest waiting for its slab copies to leave staging, [10] cluster ingest
+ * issuing slab copies, [11] kernel cycles per CTA. Tracing makes that launch
+ * synchronous. */
 int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t *count);
+
+/* ColTor, the column tournament after RowSel (Sec. 2.2, "ColTor"), with the
+ * external product of Sec. 2.5.1. For every client c < batch, log2(d1) stages
+ * halve its d1 ciphertexts (d1 a power of two, at least 2): stage s pairs the
+ * stage's inputs (2k, 2k+1) and keeps
+ *     ct_{2k} + RGSW_s [x] (ct_{2k+1} - ct_{2k}),
+ * so the result selects, bit by bit from the least significant, the column
+ * the RGSW ciphertexts encrypt. The external product takes the inverse NTT of
+ * both polynomials, rebuilds each coefficient from its limbs (CRT) centred to
+ * (-Q/2, Q/2], splits it into ell balanced base-2^22 digits (ell =
+ * gpir_coltor_gadget_digits), takes the forward NTT of the 2 ell digit
+ * polynomials and multiplies-accumulates them with the RGSW rows
+ * (row p ell + i multiplies digit i of polynomial p).
+ *   ct_dev    device, [B][d1][2][L][N]  (gpir_rowsel_batch's output layout)
+ *   rgsw_dev  device, [B][log2 d1][2 ell][2][L][N]
+ *   out_dev   device, [B][2][L][N]
+ * Everything is in NTT form A_s = sum_j a_j psi^((2s+1) j) mod q_l, natural
+ * slot order, psi = g^((q_l - 1) / 2N) with g the smallest generator of the
+ * multiplicative group mod q_l. Limits: L <= 2 and N <= 4096, else
+ * GPIR_ENOTSUP. Twiddle tables are built once per (device, N, primes); the
+ * library keeps a workspace per (device, stream) for the intermediate stages
+ * (d1/2 + d1/4 ciphertexts per client). Asynchronous. */
+int gpir_coltor(const gpir_params_t *params, uint32_t batch, uint32_t d1, const uint32_t *ct_dev,
+                const uint32_t *rgsw_dev, uint32_t *out_dev, void *stream);
+/* ell, the number of base-2^22 digits of the external product: the smallest
+ * count with 2^(22 ell) >= Q (3 for two 28-bit limbs). GPIR_EINVAL for NULL. */
+int gpir_coltor_gadget_digits(const gpir_params_t *params);
 
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return

@@ -65,6 +65,8 @@ def _load():
         "gpir_rowsel_batch_host": (I, [P, U32, P, P, I, P]),
         "gpir_rowsel_multi": (I, [ctypes.POINTER(gpir_job_t), U32, I, P]),
         "gpir_rowsel_batch_noalloc": (I, [P, U32, P, P, P]),
+        "gpir_coltor": (I, [P, U32, U32, P, P, P, P]),
+        "gpir_coltor_gadget_digits": (I, [P]),
         "gpir_graph_create": (I, [ctypes.POINTER(gpir_job_t), U32, I, P, ctypes.POINTER(P)]),
         "gpir_graph_launch": (I, [P, P]),
         "gpir_graph_destroy": (I, [P]),
@@ -213,6 +215,18 @@ def gpir_autotune(db, batch, ct_dev, out_dev, path, stream=None):
     _check(lib.gpir_autotune(db, int(batch), _ptr(ct_dev), _ptr(out_dev), int(path), _stream(stream),
                              ctypes.byref(v)), "gpir_autotune")
     return v.value
+
+
+def gpir_coltor(params, batch, d1, ct_dev, rgsw_dev, out_dev, stream=None):
+    return _check(lib.gpir_coltor(params, int(batch), int(d1), _ptr(ct_dev), _ptr(rgsw_dev), _ptr(out_dev),
+                                  _stream(stream)), "gpir_coltor")
+
+
+def gpir_coltor_gadget_digits(params):
+    r = lib.gpir_coltor_gadget_digits(params)
+    if r < 0:
+        _check(r, "gpir_coltor_gadget_digits")
+    return r
 
 
 def gpir_num_variants(path):
