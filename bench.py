@@ -349,6 +349,54 @@ class GpuWorkload:
         self.g.gpir_params_destroy(self.params)
 
 
+def run_coltor(g, torch, B=32, D1=64, steps=10, warmup=3):
+    """ColTor (the column tournament after RowSel) on the 32-client workload's
+    RowSel output shape: B clients x D1 ciphertexts, N=4096, 2 limbs, one
+    RGSW ciphertext per stage. Inputs are uniform residues drawn on the device
+    (the arithmetic does not depend on their values). Roofline: the modular
+    products of the NTT butterflies and the RGSW multiply-accumulate, each at
+    least 3 IMAD (28-bit Shoup / Barrett), against 152 SMs x 64 IMAD lanes x
+    2.07 GHz / 3."""
+    c = synth.config_shapes("c2_rowsel")
+    N, L, primes = c["N"], c["L"], list(c["primes"])
+    params = g.gpir_params_create(N, primes)
+    ell = g.gpir_coltor_gadget_digits(params)
+    stages = D1.bit_length() - 1
+    ct = torch.empty(B * D1 * 2 * L * N, dtype=torch.int32, device="cuda")
+    rgsw = torch.empty(B * stages * 2 * ell * 2 * L * N, dtype=torch.int32, device="cuda")
+    out = torch.empty(B * 2 * L * N, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(ct, ct.numel(), 0, 9, synth.TAG_COLTOR, params, N)
+    g.gpir_fill_uniform(rgsw, rgsw.numel(), 0, 9, synth.TAG_RGSW, params, N)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        g.gpir_coltor(params, B, D1, ct, rgsw, out, st.cuda_stream)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        g.gpir_coltor(params, B, D1, ct, rgsw, out, st.cuda_stream)
+    e1.record(st)
+    st.synchronize()
+    g.gpir_sync(None, 60000)
+    ms = e0.elapsed_time(e1) / steps
+    g.gpir_params_destroy(params)
+    logn = N.bit_length() - 1
+    nodes = B * (D1 - 1)
+    products = nodes * ((2 * L + 2 * ell * L) * (N // 2) * logn + 4 * ell * L * N)
+    peak = 152 * 64 * 2.07e9 / 3 / 1e12
+    achieved = products / (ms / 1e3) / 1e12
+    ct_bytes = 2 * L * N * 4
+    alg_bytes = ct_bytes * (B * D1 + B * stages * 2 * ell + B)
+    return {"workload": "ColTor after the 32-client RowSel: %d clients x %d ciphertexts, N=%d, %d limbs, ell=%d, "
+                        "%d stages" % (B, D1, N, L, ell, stages),
+            "ms": ms, "queries_s": B / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T modmul/s",
+                         "frac": achieved / peak,
+                         "note": "NTT butterflies + RGSW products (%.3g per step), 3 IMAD each, vs 152x64x2.07GHz/3; "
+                                 "HBM: %.0f MB algorithmic, %.3f ms at the measured copy bandwidth"
+                                 % (products, alg_bytes / 1e6, alg_bytes / 6652.3e9 * 1e3)}}
+
+
 def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
@@ -504,6 +552,7 @@ def main():
                               "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
+        line["coltor"] = run_coltor(g, torch)
         line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "
                                        "Poisson arrivals, toy-RLWE one-hot queries, 3 streams, max batch 32",
                            "rates": run_serving(g, torch)}
