@@ -397,6 +397,54 @@ def run_coltor(g, torch, B=32, D1=64, steps=10, warmup=3):
                                  % (products, alg_bytes / 1e6, alg_bytes / 6652.3e9 * 1e3)}}
 
 
+def run_expand(g, torch, B=32, D0=256, D1=64, steps=10, warmup=3):
+    """ExpandQuery (the query-expansion tree before RowSel) on the 32-client
+    workload: each client's query expands into D0 + log2(D1) ell ciphertexts
+    (the RowSel selection vector plus the RGSW material of ColTor), J =
+    ceil(log2 of that) stages, N=4096, 2 limbs, one evaluation key per stage.
+    Inputs are uniform residues drawn on the device. Roofline as ColTor's: the
+    modular products of the NTTs and of the key multiply-accumulate."""
+    c = synth.config_shapes("c2_rowsel")
+    N, L, primes = c["N"], c["L"], list(c["primes"])
+    params = g.gpir_params_create(N, primes)
+    ell = g.gpir_coltor_gadget_digits(params)
+    n_out = D0 + (D1.bit_length() - 1) * ell
+    J = (n_out - 1).bit_length()
+    query = torch.empty(B * 2 * L * N, dtype=torch.int32, device="cuda")
+    evk = torch.empty(B * J * ell * 2 * L * N, dtype=torch.int32, device="cuda")
+    out = torch.empty(B * n_out * 2 * L * N, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(query, query.numel(), 0, 9, synth.TAG_QUERY, params, N)
+    g.gpir_fill_uniform(evk, evk.numel(), 0, 9, synth.TAG_EVK, params, N)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        g.gpir_expand_query(params, B, J, n_out, query, evk, out, st.cuda_stream)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        g.gpir_expand_query(params, B, J, n_out, query, evk, out, st.cuda_stream)
+    e1.record(st)
+    st.synchronize()
+    g.gpir_sync(None, 60000)
+    ms = e0.elapsed_time(e1) / steps
+    g.gpir_params_destroy(params)
+    logn = N.bit_length() - 1
+    nodes = B * sum(min(1 << j, n_out) for j in range(J))
+    products = nodes * ((L + ell * L) * (N // 2) * logn + 2 * ell * L * N + 2 * L * N)
+    peak = 152 * 64 * 2.07e9 / 3 / 1e12
+    achieved = products / (ms / 1e3) / 1e12
+    ct_bytes = 2 * L * N * 4
+    alg_bytes = ct_bytes * (B + B * J * ell + B * n_out)
+    return {"workload": "ExpandQuery before the 32-client RowSel: %d clients, %d outputs each (%d + %d x %d), "
+                        "%d stages, N=%d, %d limbs" % (B, n_out, D0, D1.bit_length() - 1, ell, J, N, L),
+            "ms": ms, "queries_s": B / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T modmul/s",
+                         "frac": achieved / peak,
+                         "note": "NTT butterflies + key products + X^-2^j products (%.3g per step), 3 IMAD each, "
+                                 "vs 152x64x2.07GHz/3; HBM: %.0f MB algorithmic, %.3f ms at the measured copy "
+                                 "bandwidth" % (products, alg_bytes / 1e6, alg_bytes / 6652.3e9 * 1e3)}}
+
+
 def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
@@ -552,6 +600,7 @@ def main():
                               "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
+        line["expand_query"] = run_expand(g, torch)
         line["coltor"] = run_coltor(g, torch)
         line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "
                                        "Poisson arrivals, toy-RLWE one-hot queries, 3 streams, max batch 32",

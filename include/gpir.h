@@ -251,15 +251,37 @@ int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t
  *   out_dev   device, [B][2][L][N]
  * Everything is in NTT form A_s = sum_j a_j psi^((2s+1) j) mod q_l, natural
  * slot order, psi = g^((q_l - 1) / 2N) with g the smallest generator of the
- * multiplicative group mod q_l. Limits: L <= 2 and N <= 4096, else
+ * multiplicative group mod q_l. Limits: L <= 2 and 16 <= N <= 4096, else
  * GPIR_ENOTSUP. Twiddle tables are built once per (device, N, primes); the
  * library keeps a workspace per (device, stream) for the intermediate stages
- * (d1/2 + d1/4 ciphertexts per client). Asynchronous. */
+ * (d1/2 + d1/4 ciphertexts per client). ct_dev is not modified. Asynchronous. */
 int gpir_coltor(const gpir_params_t *params, uint32_t batch, uint32_t d1, const uint32_t *ct_dev,
                 const uint32_t *rgsw_dev, uint32_t *out_dev, void *stream);
 /* ell, the number of base-2^22 digits of the external product: the smallest
  * count with 2^(22 ell) >= Q (3 for two 28-bit limbs). GPIR_EINVAL for NULL. */
 int gpir_coltor_gadget_digits(const gpir_params_t *params);
+
+/* ExpandQuery, the query-expansion tree before RowSel (Sec. 2.2,
+ * "ExpandQuery"), with the homomorphic substitution Subs of Sec. 2.5.1. For
+ * every client c < batch, `stages` = J stages turn its query ciphertext into
+ * 2^J ciphertexts, of which the first n_out (1 <= n_out <= 2^J) are written.
+ * Stage j maps the list [c_0 .. c_{2^j - 1}] to a list twice as long: node k
+ * computes t = Subs(c_k, N/2^j + 1, evk_j) and writes c_k + t at index k and
+ * X^(-2^j) (c_k - t) at index k + 2^j. Subs(ct = (a, b), k) applies X -> X^k
+ * to a and b and switches keys with Dcp on the substituted a (inverse NTT,
+ * CRT centred to (-Q/2, Q/2], ell balanced base-2^22 digits as in
+ * gpir_coltor, forward NTT): t = (sum_i d_i (.) evk[i][0],
+ * tau(b) + sum_i d_i (.) evk[i][1]). If the query encrypts m(X), output r
+ * encrypts 2^J sum_i m_{2^J i + r} X^(2^J i).
+ *   query_dev device, [B][2][L][N]
+ *   evk_dev   device, [B][J][ell][2][L][N] (may be NULL when J = 0)
+ *   out_dev   device, [B][n_out][2][L][N]; must not overlap query_dev. The
+ *             tree runs in place in it: no other workspace.
+ * NTT form and limits as gpir_coltor; J <= log2 N (else GPIR_EINVAL: X^k with
+ * k = N/2^j + 1 is an automorphism only for j < log2 N). J = 0 copies the
+ * query. query_dev and evk_dev are not modified. Asynchronous. */
+int gpir_expand_query(const gpir_params_t *params, uint32_t batch, uint32_t stages, uint32_t n_out,
+                      const uint32_t *query_dev, const uint32_t *evk_dev, uint32_t *out_dev, void *stream);
 
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return

@@ -67,6 +67,7 @@ def _load():
         "gpir_rowsel_batch_noalloc": (I, [P, U32, P, P, P]),
         "gpir_coltor": (I, [P, U32, U32, P, P, P, P]),
         "gpir_coltor_gadget_digits": (I, [P]),
+        "gpir_expand_query": (I, [P, U32, U32, U32, P, P, P, P]),
         "gpir_graph_create": (I, [ctypes.POINTER(gpir_job_t), U32, I, P, ctypes.POINTER(P)]),
         "gpir_graph_launch": (I, [P, P]),
         "gpir_graph_destroy": (I, [P]),
@@ -220,6 +221,12 @@ def gpir_autotune(db, batch, ct_dev, out_dev, path, stream=None):
 def gpir_coltor(params, batch, d1, ct_dev, rgsw_dev, out_dev, stream=None):
     return _check(lib.gpir_coltor(params, int(batch), int(d1), _ptr(ct_dev), _ptr(rgsw_dev), _ptr(out_dev),
                                   _stream(stream)), "gpir_coltor")
+
+
+def gpir_expand_query(params, batch, stages, n_out, query_dev, evk_dev, out_dev, stream=None):
+    return _check(lib.gpir_expand_query(params, int(batch), int(stages), int(n_out), _ptr(query_dev),
+                                        _ptr(evk_dev), _ptr(out_dev),
+                                        _stream(stream)), "gpir_expand_query")
 
 
 def gpir_coltor_gadget_digits(params):

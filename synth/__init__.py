@@ -18,9 +18,12 @@ from .gen import (GAMMA, mix64, stream_key, uniform_u64, uniform_residues, resid
                   uniform_u64_at, ct_slots, db_slots,
                   ct_tensor, db_tensor, TAG_DB, TAG_CT, TAG_SECRET, TAG_MASK,
                   toy_rlwe_selection, config_shapes, CONFIGS, PRIMES_28,
-                  TAG_RGSW, TAG_COLTOR, TAG_RECORD, toy_rgsw, toy_coltor_inputs)
+                  TAG_RGSW, TAG_COLTOR, TAG_RECORD, TAG_EVK, TAG_QUERY, TAG_MESSAGE,
+                  toy_rgsw, toy_coltor_inputs)
 
 __all__ = ["GAMMA", "mix64", "stream_key", "uniform_u64", "uniform_residues", "residues_at",
            "uniform_u64_at", "ct_slots", "db_slots",
            "ct_tensor", "db_tensor", "TAG_DB", "TAG_CT", "TAG_SECRET", "TAG_MASK",
-           "toy_rlwe_selection", "config_shapes", "CONFIGS", "PRIMES_28"]
+           "toy_rlwe_selection", "config_shapes", "CONFIGS", "PRIMES_28",
+           "TAG_RGSW", "TAG_COLTOR", "TAG_RECORD", "TAG_EVK", "TAG_QUERY", "TAG_MESSAGE",
+           "toy_rgsw", "toy_coltor_inputs"]

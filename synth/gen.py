@@ -15,6 +15,9 @@ TAG_MASK = 4      # toy RLWE uniform "a" polynomials
 TAG_RGSW = 5      # toy RGSW uniform "a" polynomials (ColTor inputs)
 TAG_COLTOR = 6    # toy RLWE uniform "a" polynomials of ColTor's input ciphertexts
 TAG_RECORD = 7    # records (plaintext polynomials) those ciphertexts encrypt
+TAG_EVK = 8       # toy evaluation-key uniform polynomials (ExpandQuery inputs)
+TAG_QUERY = 9     # query ciphertexts (ExpandQuery inputs)
+TAG_MESSAGE = 10  # toy query message coefficients
 
 # The two largest primes below 2^28 that are 1 mod 8192 (so NTT-friendly for
 # every N <= 4096): 0xFFF0001 and 0xFFEE001.

@@ -12,9 +12,9 @@ import numpy as np
 import oracle
 import synth
 
-TAG_EVK = 8        # toy evaluation-key uniform polynomials
-TAG_QUERY = 9      # toy query mask polynomial
-TAG_MESSAGE = 10   # toy query message coefficients
+TAG_EVK = synth.TAG_EVK
+TAG_QUERY = synth.TAG_QUERY
+TAG_MESSAGE = synth.TAG_MESSAGE
 
 
 def slot_perm(N: int, k: int) -> np.ndarray:
