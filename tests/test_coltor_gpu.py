@@ -1,5 +1,8 @@
 """GPU ColTor vs the CPU oracle, bit-exact (modular integer work: tolerance 0),
-plus decryption checks of the tournament at full ring size.
+plus decryption checks of the tournament at full ring size. The library picks
+one of two stage kernels per stage by node count (a cluster per node split by
+limb, or by polynomial and limb when the nodes are few); the shapes below
+reach both.
 
 All calls go through the C ABI (libgpir.so) via the ctypes binding."""
 
@@ -44,6 +47,8 @@ SHAPES = [
     (1, 16, 2, 512),           # four stages (ping-pong workspace), N = one CTA's width
     (2, 2, 2, 1024),           # points per thread > 1
     (1, 2, 2, 4096),           # the workload ring size
+    (10, 64, 2, 32),           # >= 2 CTAs per SM of nodes: the limb kernel in the early stages, the split one late
+    (10, 64, 1, 32),           # the same with one limb
 ]
 
 

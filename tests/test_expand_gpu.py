@@ -1,6 +1,8 @@
 """GPU ExpandQuery vs the CPU oracle, bit-exact (modular integer work: tolerance
 0), plus decryption checks at full ring size and the three server phases
-chained on the GPU.
+chained on the GPU. The library picks one of two stage kernels per stage by
+node count (a cluster per node split by limb, or by limb and digit when the
+nodes are few); the shapes below reach both.
 
 All calls go through the C ABI (libgpir.so) via the ctypes binding."""
 
@@ -46,6 +48,8 @@ SHAPES = [
     (2, 4, 11, 2, 512),         # ragged n_out over four stages
     (1, 3, 5, 2, 128),          # logn = 7: a radix-2 middle round
     (1, 2, 4, 2, 4096),         # the workload ring size
+    (20, 5, 32, 2, 32),         # >= 2 CTAs per SM of nodes in the last stage: the limb kernel there, the split one before
+    (20, 5, 29, 1, 32),         # the same with one limb, ragged
 ]
 
 
