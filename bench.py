@@ -445,6 +445,57 @@ def run_expand(g, torch, B=32, D0=256, D1=64, steps=10, warmup=3):
                                  "bandwidth" % (products, alg_bytes / 1e6, alg_bytes / 6652.3e9 * 1e3)}}
 
 
+def run_pir_pipeline(g, torch, steps=5, warmup=3):
+    """The whole server step on the 32-client workload through gpir_pir_batch:
+    ExpandQuery (J = 8 stages, 256 selection ciphertexts per client), RowSel
+    against the resident 512 MiB DB (tensor-core path), ColTor over the 64
+    results. Inputs are uniform residues drawn on the device; per-phase device
+    times come from the library's launch trace."""
+    eng = GpuWorkload(g, torch, workload_shape("c2_rowsel"), 4)
+    w, params, N, L = eng.w, eng.params, eng.w["N"], eng.w["L"]
+    B, D0, D1 = w["B"], w["D0"], w["D1"]
+    ell = g.gpir_coltor_gadget_digits(params)
+    J = (D0 - 1).bit_length()
+    stages = D1.bit_length() - 1
+    ctw = 2 * L * N
+    query = torch.empty(B * ctw, dtype=torch.int32, device="cuda")
+    evk = torch.empty(B * J * ell * ctw, dtype=torch.int32, device="cuda")
+    rgsw = torch.empty(B * stages * 2 * ell * ctw, dtype=torch.int32, device="cuda")
+    sel = torch.empty(B * D0 * ctw, dtype=torch.int32, device="cuda")
+    rows = torch.empty(B * D1 * ctw, dtype=torch.int32, device="cuda")
+    out = torch.empty(B * ctw, dtype=torch.int32, device="cuda")
+    g.gpir_fill_uniform(query, query.numel(), 0, 9, synth.TAG_QUERY, params, N)
+    g.gpir_fill_uniform(evk, evk.numel(), 0, 9, synth.TAG_EVK, params, N)
+    g.gpir_fill_uniform(rgsw, rgsw.numel(), 0, 9, synth.TAG_RGSW, params, N)
+    st = torch.cuda.current_stream()
+    call = lambda: g.gpir_pir_batch(eng.h, B, J, query, evk, rgsw, sel, rows, out, 4, st.cuda_stream)
+    for _ in range(warmup):
+        call()
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        call()
+    e1.record(st)
+    st.synchronize()
+    g.gpir_sync(None, 60000)
+    ms = e0.elapsed_time(e1) / steps
+    g.gpir_trace_enable(True)
+    g.gpir_trace_read()
+    call()
+    st.synchronize()
+    recs = g.gpir_trace_read()
+    g.gpir_trace_enable(False)
+    phase = {"expand_query": 0.0, "rowsel": 0.0, "coltor": 0.0}
+    for name, t in recs:
+        key = "expand_query" if name.startswith("expand") else ("coltor" if name.startswith("coltor") else "rowsel")
+        phase[key] += t
+    eng.close()
+    return {"workload": "one server step, 32 clients: ExpandQuery (%d stages, %d selection cts) -> RowSel "
+                        "(%dx%d DB, tensor core) -> ColTor (%d stages), N=%d, %d limbs" % (J, D0, D0, D1, stages, N, L),
+            "ms": ms, "queries_s": B / (ms / 1e3), "phase_ms": {k: round(v, 4) for k, v in phase.items()}}
+
+
 def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
@@ -600,6 +651,8 @@ def main():
                               "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
+        if args.workload == "c2_rowsel":
+            line["pir_pipeline"] = run_pir_pipeline(g, torch)
         line["expand_query"] = run_expand(g, torch)
         line["coltor"] = run_coltor(g, torch)
         line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "

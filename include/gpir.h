@@ -283,6 +283,25 @@ int gpir_coltor_gadget_digits(const gpir_params_t *params);
 int gpir_expand_query(const gpir_params_t *params, uint32_t batch, uint32_t stages, uint32_t n_out,
                       const uint32_t *query_dev, const uint32_t *evk_dev, uint32_t *out_dev, void *stream);
 
+/* One server step of the PIR protocol (Sec. 2.2, the three phases) for
+ * `batch` clients against `db`, on `stream`:
+ *   1. gpir_expand_query: each query ciphertext expands, in `stages` = J
+ *      stages (D0 <= 2^J), into the D0 selection ciphertexts, written to sel_dev;
+ *   2. gpir_rowsel_batch(db, batch, sel_dev, rows_dev, path): D1 ciphertexts;
+ *   3. gpir_coltor over those D1 (a power of two, at least 2): out_dev.
+ *   query_dev device, [B][2][L][N]
+ *   evk_dev   device, [B][J][ell][2][L][N]
+ *   rgsw_dev  device, [B][log2 D1][2 ell][2][L][N]
+ *   sel_dev   device, [B][D0][2][L][N]: caller-owned buffer for the expanded ciphertexts
+ *   rows_dev  device, [B][D1][2][L][N]: caller-owned buffer for RowSel's output
+ *   out_dev   device, [B][2][L][N]
+ * No buffer may overlap another. Each phase's limits and workspaces are those
+ * of its own call; the first error is returned and later phases are not
+ * enqueued. Asynchronous. */
+int gpir_pir_batch(const gpir_db_t *db, uint32_t batch, uint32_t stages, const uint32_t *query_dev,
+                   const uint32_t *evk_dev, const uint32_t *rgsw_dev, uint32_t *sel_dev, uint32_t *rows_dev,
+                   uint32_t *out_dev, int path, void *stream);
+
 const char *gpir_strerror(int code);
 /* Text of the last CUDA runtime error that made a call of this thread return
  * GPIR_ECUDA or GPIR_ENOMEM ("no error" if none). */

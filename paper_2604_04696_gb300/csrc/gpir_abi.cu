@@ -339,6 +339,26 @@ int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_de
   return dispatch(db, batch, ct_dev, out_dev, p, pick_variant(db, batch, p), (cudaStream_t)stream);
 }
 
+int gpir_pir_batch(const gpir_db_t *db, uint32_t batch, uint32_t stages, const uint32_t *query_dev,
+                   const uint32_t *evk_dev, const uint32_t *rgsw_dev, uint32_t *sel_dev, uint32_t *rows_dev,
+                   uint32_t *out_dev, int path, void *stream) {
+  if (!db || batch == 0 || !query_dev || !rgsw_dev || !sel_dev || !rows_dev || !out_dev) return GPIR_EINVAL;
+  if (db->d1 < 2 || (db->d1 & (db->d1 - 1)) != 0) return GPIR_EINVAL;
+  if (stages >= 32 || db->d0 > (1u << stages)) return GPIR_EINVAL;
+  const size_t ctw = (size_t)2 * db->params.num_limbs * db->params.n * 4;
+  const uintptr_t q0 = (uintptr_t)query_dev, q1 = q0 + batch * ctw;
+  const uintptr_t s0 = (uintptr_t)sel_dev, s1 = s0 + (size_t)batch * db->d0 * ctw;
+  const uintptr_t r0 = (uintptr_t)rows_dev, r1 = r0 + (size_t)batch * db->d1 * ctw;
+  const uintptr_t o0 = (uintptr_t)out_dev, o1 = o0 + batch * ctw;
+  if ((q0 < s1 && s0 < q1) || (s0 < r1 && r0 < s1) || (r0 < o1 && o0 < r1) || (s0 < o1 && o0 < s1))
+    return GPIR_EINVAL;
+  int rc = gpir_expand_query(&db->params, batch, stages, db->d0, query_dev, evk_dev, sel_dev, stream);
+  if (rc != GPIR_OK) return rc;
+  rc = gpir_rowsel_batch(db, batch, sel_dev, rows_dev, path, stream);
+  if (rc != GPIR_OK) return rc;
+  return gpir_coltor(&db->params, batch, db->d1, rows_dev, rgsw_dev, out_dev, stream);
+}
+
 int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t *ct_host, uint32_t *out_host,
                            int path, void *stream) {
   if (!db_c || !ct_host || !out_host || batch == 0) return GPIR_EINVAL;

@@ -68,6 +68,7 @@ def _load():
         "gpir_coltor": (I, [P, U32, U32, P, P, P, P]),
         "gpir_coltor_gadget_digits": (I, [P]),
         "gpir_expand_query": (I, [P, U32, U32, U32, P, P, P, P]),
+        "gpir_pir_batch": (I, [P, U32, U32, P, P, P, P, P, P, I, P]),
         "gpir_graph_create": (I, [ctypes.POINTER(gpir_job_t), U32, I, P, ctypes.POINTER(P)]),
         "gpir_graph_launch": (I, [P, P]),
         "gpir_graph_destroy": (I, [P]),
@@ -227,6 +228,12 @@ def gpir_expand_query(params, batch, stages, n_out, query_dev, evk_dev, out_dev,
     return _check(lib.gpir_expand_query(params, int(batch), int(stages), int(n_out), _ptr(query_dev),
                                         _ptr(evk_dev), _ptr(out_dev),
                                         _stream(stream)), "gpir_expand_query")
+
+
+def gpir_pir_batch(db, batch, stages, query_dev, evk_dev, rgsw_dev, sel_dev, rows_dev, out_dev, path=0, stream=None):
+    return _check(lib.gpir_pir_batch(db, int(batch), int(stages), _ptr(query_dev), _ptr(evk_dev), _ptr(rgsw_dev),
+                                     _ptr(sel_dev), _ptr(rows_dev), _ptr(out_dev), int(path), _stream(stream)),
+                  "gpir_pir_batch")
 
 
 def gpir_coltor_gadget_digits(params):

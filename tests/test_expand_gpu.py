@@ -173,3 +173,59 @@ def test_expand_argument_errors(g):
                 g.GPIR_ENOTSUP
         finally:
             g.gpir_params_destroy(p3)
+
+
+def test_pir_batch_equals_the_three_calls_and_decrypts(g):
+    """gpir_pir_batch (ExpandQuery -> RowSel -> ColTor in one call, caller-owned
+    intermediate buffers) returns exactly what the three separate calls return,
+    for every RowSel path, and decrypts to 2^J DB[i*][j*]."""
+    import torch
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    N, L, D0, D1, J = 1024, 2, 48, 4, 6
+    primes = P28
+    ell = oracle.gadget_digits(primes)
+    db = synth.uniform_residues(911, synth.TAG_DB, (D0, D1, L, N), primes, limb_axis=2)
+    picks = [(47, 1), (0, 3)]
+    h = DbHandle(g, db, N, primes, path_mask=0)
+    try:
+        queries, evks, secrets, rgsws = [], [], [], []
+        for c, (i, j) in enumerate(picks):
+            q_, evk, s, _ = eu.toy_expand_inputs(920 + c, J, L, N, primes, ell)
+            for l, q in enumerate(primes):
+                M = oracle.monomial_ntt(i, q, N)
+                q_[1, l] = ((q_[0, l].astype(np.uint64) * s[l].astype(np.uint64) + M) % np.uint64(q)).astype(np.uint32)
+            queries.append(q_)
+            evks.append(evk)
+            secrets.append(s)
+            rgsws.append(np.stack([synth.toy_rgsw(920 + c, st, (j >> st) & 1, s, L, N, primes, ell)
+                                   for st in range(D1.bit_length() - 1)]))
+        B = len(picks)
+        qd, ed, rd = to_dev(np.stack(queries)), to_dev(np.stack(evks)), to_dev(np.stack(rgsws))
+        sel = torch.full((B, D0, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        rows = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        ref = torch.full((B, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        g.gpir_expand_query(h.params, B, J, D0, qd, ed, sel)
+        g.gpir_rowsel_batch(h.h, B, sel, rows, g.GPIR_PATH_CUDACORE)
+        g.gpir_coltor(h.params, B, D1, rows, rd, ref)
+        torch.cuda.synchronize()
+        want = to_host(ref)
+        for path in (g.GPIR_PATH_CUDACORE, g.GPIR_PATH_IMMA, g.GPIR_PATH_TC):
+            out = torch.full((B, 2, L, N), -1, dtype=torch.int32, device="cuda")
+            sel.fill_(-1)
+            rows.fill_(-1)
+            g.gpir_pir_batch(h.h, B, J, qd, ed, rd, sel, rows, out, path)
+            torch.cuda.synchronize()
+            g.gpir_sync(None, 20000)
+            assert np.array_equal(to_host(out), want), "path %d" % path
+        assert g.lib.gpir_pir_batch(h.h, B, 5, qd.data_ptr(), ed.data_ptr(), rd.data_ptr(), sel.data_ptr(),
+                                    rows.data_ptr(), out.data_ptr(), 0, None) == g.GPIR_EINVAL   # 2^5 < D0
+        assert g.lib.gpir_pir_batch(h.h, B, J, qd.data_ptr(), ed.data_ptr(), rd.data_ptr(), sel.data_ptr(),
+                                    sel.data_ptr(), out.data_ptr(), 0, None) == g.GPIR_EINVAL   # overlap
+    finally:
+        h.close()
+    for c, (i, j) in enumerate(picks):
+        for l, q in enumerate(primes):
+            a = want[c, 0, l].astype(np.uint64)
+            b = want[c, 1, l].astype(np.uint64)
+            m = (b + np.uint64(q) - (a * secrets[c][l].astype(np.uint64)) % np.uint64(q)) % np.uint64(q)
+            assert np.array_equal(m, (db[i, j, l].astype(np.uint64) * np.uint64(1 << J)) % np.uint64(q))
