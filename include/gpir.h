@@ -254,7 +254,9 @@ int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t
  * multiplicative group mod q_l. Limits: L <= 2 and 16 <= N <= 4096, else
  * GPIR_ENOTSUP. Twiddle tables are built once per (device, N, primes); the
  * library keeps a workspace per (device, stream) for the intermediate stages
- * (d1/2 + d1/4 ciphertexts per client). ct_dev is not modified. Asynchronous. */
+ * (d1/2 + d1/4 ciphertexts per client). ct_dev is not modified; out_dev must
+ * not overlap it (GPIR_EINVAL). Argument errors are returned before any CUDA
+ * call. Asynchronous. */
 int gpir_coltor(const gpir_params_t *params, uint32_t batch, uint32_t d1, const uint32_t *ct_dev,
                 const uint32_t *rgsw_dev, uint32_t *out_dev, void *stream);
 /* ell, the number of base-2^22 digits of the external product: the smallest
@@ -279,7 +281,8 @@ int gpir_coltor_gadget_digits(const gpir_params_t *params);
  *             tree runs in place in it: no other workspace.
  * NTT form and limits as gpir_coltor; J <= log2 N (else GPIR_EINVAL: X^k with
  * k = N/2^j + 1 is an automorphism only for j < log2 N). J = 0 copies the
- * query. query_dev and evk_dev are not modified. Asynchronous. */
+ * query. query_dev and evk_dev are not modified. Argument errors are returned
+ * before any CUDA call. Asynchronous. */
 int gpir_expand_query(const gpir_params_t *params, uint32_t batch, uint32_t stages, uint32_t n_out,
                       const uint32_t *query_dev, const uint32_t *evk_dev, uint32_t *out_dev, void *stream);
 

@@ -387,8 +387,17 @@ extern "C" int gpir_coltor_gadget_digits(const gpir_params_t *params) {
 extern "C" int gpir_coltor(const gpir_params_t *params, uint32_t batch, uint32_t d1, const uint32_t *ct_dev,
                            const uint32_t *rgsw_dev, uint32_t *out_dev, void *stream) {
   using namespace gpir;
+  // every argument is checked here, on the host, before any CUDA call
   if (!params || !ct_dev || !rgsw_dev || !out_dev || batch == 0 || d1 < 2 || (d1 & (d1 - 1)) != 0)
     return GPIR_EINVAL;
+  if (params->num_limbs < 1 || params->num_limbs > ntt::MAX_LIMBS || params->n < ntt::MIN_N || params->n > ntt::MAX_N)
+    return GPIR_ENOTSUP;
+  {
+    const size_t ctw = (size_t)2 * params->num_limbs * params->n * 4;
+    const uintptr_t i0 = (uintptr_t)ct_dev, i1 = i0 + (size_t)batch * d1 * ctw;
+    const uintptr_t o0 = (uintptr_t)out_dev, o1 = o0 + batch * ctw;
+    if (i0 < o1 && o0 < i1) return GPIR_EINVAL;   // the last stage reads ct_dev's results while writing out_dev
+  }
   ntt::Ring ring;
   int rc = ring_tables(params, &ring);
   if (rc != GPIR_OK) return rc;

@@ -387,14 +387,25 @@ extern "C" int gpir_expand_query(const gpir_params_t *params, uint32_t batch, ui
                                  const uint32_t *query_dev, const uint32_t *evk_dev, uint32_t *out_dev,
                                  void *stream) {
   using namespace gpir;
+  // every argument is checked here, on the host, before any CUDA call
   if (!params || !query_dev || !out_dev || batch == 0 || n_out == 0) return GPIR_EINVAL;
   if (stages > 0 && !evk_dev) return GPIR_EINVAL;
+  if (params->num_limbs < 1 || params->num_limbs > ntt::MAX_LIMBS || params->n < ntt::MIN_N || params->n > ntt::MAX_N)
+    return GPIR_ENOTSUP;
+  uint32_t logn = 0;
+  while ((1u << logn) < params->n) ++logn;
+  // tau_k with k = N / 2^j + 1 is an automorphism (k odd) only for j < log2 N
+  if (stages > logn || n_out > (1u << stages)) return GPIR_EINVAL;
+  {
+    const size_t ctw = (size_t)2 * params->num_limbs * params->n * 4;
+    const uintptr_t q0 = (uintptr_t)query_dev, q1 = q0 + batch * ctw;
+    const uintptr_t o0 = (uintptr_t)out_dev, o1 = o0 + (size_t)batch * n_out * ctw;
+    if (q0 < o1 && o0 < q1) return GPIR_EINVAL;   // the tree runs in place in out_dev
+  }
   ntt::Ring ring;
   int rc = ring_tables(params, &ring);
   if (rc != GPIR_OK) return rc;
   const uint32_t L = ring.L, N = ring.N;
-  // tau_k with k = N / 2^j + 1 is an automorphism (k odd) only for j < log2 N
-  if (stages > ring.logn || (stages < 32 && n_out > (1u << stages))) return GPIR_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t ct_words = (size_t)2 * L * N;
   if (stages == 0) {

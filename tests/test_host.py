@@ -149,3 +149,34 @@ def test_slot_sampling_matches_full_tensors():
     for k, (l, t) in enumerate(slots):
         assert np.array_equal(cs[..., k], ct[:, :, :, l, t])
         assert np.array_equal(ds[..., k], db[:, :, l, t])
+
+
+def test_tree_and_pipeline_argument_errors_on_the_host(g):
+    """ColTor, ExpandQuery and the one-call server step check their arguments
+    before any CUDA call (no GPU here): fake, non-overlapping addresses."""
+    P28 = [268369921, 268361729]
+    p = g.gpir_params_create(64, P28)
+    try:
+        A, B, C = 1 << 40, 2 << 40, 3 << 40
+        col, exq = g.lib.gpir_coltor, g.lib.gpir_expand_query
+        for d1 in (0, 1, 3, 6):
+            assert col(p, 1, d1, A, B, C, None) == g.GPIR_EINVAL
+        assert col(p, 0, 4, A, B, C, None) == g.GPIR_EINVAL
+        assert col(p, 1, 4, None, B, C, None) == g.GPIR_EINVAL
+        assert col(p, 1, 4, A, B, A + 64, None) == g.GPIR_EINVAL            # out inside the input
+        assert exq(p, 1, 2, 5, A, B, C, None) == g.GPIR_EINVAL              # n_out > 2^J
+        assert exq(p, 1, 2, 0, A, B, C, None) == g.GPIR_EINVAL
+        assert exq(p, 0, 2, 4, A, B, C, None) == g.GPIR_EINVAL
+        assert exq(p, 1, 7, 4, A, B, C, None) == g.GPIR_EINVAL              # J > log2 N
+        assert exq(p, 1, 2, 4, A, None, C, None) == g.GPIR_EINVAL           # no keys
+        assert exq(p, 1, 2, 4, A, B, A + 64, None) == g.GPIR_EINVAL         # out overlaps the query
+        assert g.lib.gpir_pir_batch(None, 1, 2, A, B, C, A, B, C, 0, None) == g.GPIR_EINVAL
+    finally:
+        g.gpir_params_destroy(p)
+    for n, primes in [(64, P28 + [268271617]), (8, P28[:1]), (8192, [786433])]:
+        p3 = g.gpir_params_create(n, primes)
+        try:
+            assert g.lib.gpir_coltor(p3, 1, 2, 1 << 40, 2 << 40, 3 << 40, None) == g.GPIR_ENOTSUP
+            assert g.lib.gpir_expand_query(p3, 1, 1, 2, 1 << 40, 2 << 40, 3 << 40, None) == g.GPIR_ENOTSUP
+        finally:
+            g.gpir_params_destroy(p3)
