@@ -185,3 +185,26 @@ def test_n_out_is_a_prefix():
         assert np.array_equal(oracle.expand_query(query, evk, primes, n_out), full[:n_out])
     with pytest.raises(ValueError):
         oracle.expand_query(query, evk, primes, 9)
+
+
+@pytest.mark.parametrize("istar,jstar", [(0, 0), (5, 3), (7, 1)])
+def test_three_phases_return_the_scaled_record(istar, jstar):
+    """ExpandQuery of a query encrypting X^(i*) gives the one-hot selection
+    vector (scaled by 2^J), RowSel selects row i*, ColTor with RGSW bits of j*
+    selects column j*: the result decrypts to 2^J DB[i*][j*] (noiseless toy
+    keys, N = 16)."""
+    primes = PRIMES
+    N, L, D0, D1, J = 16, 2, 8, 4, 3
+    ell = oracle.gadget_digits(primes)
+    db = synth.uniform_residues(51, synth.TAG_DB, (D0, D1, L, N), primes, limb_axis=2)
+    query, evk, s, _ = eu.toy_expand_inputs(52, J, L, N, primes, ell)
+    for l, q in enumerate(primes):
+        M = oracle.monomial_ntt(istar, q, N)
+        query[1, l] = ((query[0, l].astype(np.uint64) * s[l].astype(np.uint64) + M) % np.uint64(q)).astype(np.uint32)
+    sel = oracle.expand_query(query, evk, primes, D0)                    # [D0][2][L][N]
+    rows = oracle.rowsel(sel[None], db, primes)[0]                        # [D1][2][L][N]
+    rgsw = np.stack([synth.toy_rgsw(53, st, (jstar >> st) & 1, s, L, N, primes, ell) for st in range(2)])
+    out = oracle.coltor(rows, rgsw, primes)
+    for l, q in enumerate(primes):
+        ph = [(int(bb) - int(aa) * int(ss)) % q for aa, bb, ss in zip(out[0][l], out[1][l], s[l])]
+        assert ph == [((1 << J) * int(x)) % q for x in db[istar][jstar][l]]
