@@ -115,10 +115,14 @@ int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_de
                       uint32_t *out_dev, int path, void *stream);
 
 /* Same computation with HOST buffers: copies ct host->device, runs RowSel and
- * copies out device->host, all on `stream`, through a device workspace the
- * handle owns (grown on demand; GPIR_ENOMEM if that fails). Returns after
- * enqueueing; the host output is valid after gpir_sync(stream). Not safe to
- * call concurrently on the same handle from several streams. */
+ * copies out device->host, through a device workspace the handle owns (grown
+ * on demand; GPIR_ENOMEM if that fails). Batches of 16 or more go in client
+ * chunks so that uploads, RowSel and downloads overlap (two internal copy
+ * streams per device, ordered after the work already in `stream`; `stream`
+ * waits on the last download). Returns after enqueueing; the host output is
+ * valid after gpir_sync(stream). For full copy speed the host buffers should
+ * be pinned. Not safe to call concurrently on the same handle from several
+ * streams. */
 int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_host,
                            uint32_t *out_host, int path, void *stream);
 

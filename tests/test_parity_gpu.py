@@ -228,6 +228,33 @@ def test_host_entry_point_matches_device(g):
         h.close()
 
 
+def test_host_entry_point_chunked_pipeline(g):
+    """Batches of 16 or more go through the chunked copy pipeline (uploads,
+    RowSel and downloads overlapped over three streams): uneven chunks, pinned
+    and pageable buffers, every path, two calls back to back without a sync."""
+    import torch
+    from tests.gpu_util import DbHandle, make_problem
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 19, 37, 21, 2, 128
+    ct, db = make_problem(41, B, D0, D1, L, N, primes)
+    ct2, _ = make_problem(42, B, D0, D1, L, N, primes)
+    want, want2 = oracle.rowsel(ct, db, list(primes)), oracle.rowsel(ct2, db, list(primes))
+    h = DbHandle(g, db, N, primes, path_mask=0)
+    try:
+        for path in [p for p in (0, 1, 2, 4) if p == 0 or g.gpir_num_variants(p) > 0]:
+            ct_p = torch.from_numpy(ct.view(np.int32).copy()).pin_memory()
+            ct2_p = torch.from_numpy(ct2.view(np.int32).copy()).pin_memory()
+            out_p = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32).pin_memory()
+            out2_np = np.zeros((B, D1, 2, L, N), dtype=np.uint32)
+            g.gpir_rowsel_batch_host(h.h, B, ct_p, out_p, path)
+            g.gpir_rowsel_batch_host(h.h, B, np.ascontiguousarray(ct2), out2_np, path)
+            g.gpir_sync(None, 20000)
+            assert np.array_equal(out_p.numpy().view(np.uint32), want), "path %d, pinned" % path
+            assert np.array_equal(out2_np, want2), "path %d, pageable" % path
+    finally:
+        h.close()
+
+
 def test_upload_rejects_out_of_range_residue(g):
     import torch
     from tests.gpu_util import to_dev
