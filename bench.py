@@ -501,6 +501,10 @@ def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
     one-hot selection drawn from a per-DB pool; p50/p99 latency and queries/s."""
     from paper_2604_04696_gb300.server import Request, ResidentDb, Server, poisson_arrivals, toy_rlwe_query
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()   # the earlier sections' cached buffers go back before the DBs are made resident
     c = synth.config_shapes("c5_serving")
     N, L, primes = c["N"], c["L"], list(c["primes"])
     params = g.gpir_params_create(N, primes)

@@ -18,6 +18,7 @@ reduction across clients, so each output depends only on its own request.
 """
 
 import collections
+import gc
 import time
 
 import numpy as np
@@ -67,7 +68,18 @@ class Server:
         """Serve `requests` (sorted by arrival time, seconds from start; each
         request's `query` is a pinned host int32 tensor of its database's ct
         shape). Returns a stats dict; fills request timestamps (and outputs
-        when keep_outputs)."""
+        when keep_outputs). Python's cyclic garbage collector is paused while
+        the loop runs: a collection pause in the polling loop delays every
+        request in flight."""
+        gc_was_on = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, timeout_s)
+        finally:
+            if gc_was_on:
+                gc.enable()
+
+    def _run(self, requests, timeout_s):
         reqs = list(requests)
         n = len(reqs)
         waiting = collections.deque()
