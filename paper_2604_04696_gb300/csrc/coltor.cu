@@ -14,26 +14,31 @@
 //   3. forward NTT of the 2 ell digit polynomials (digits reduced mod q_l);
 //   4. out_r = sum_{p, i} NTT(d_{p,i}) (.) rgsw[p ell + i][r], r in {0, 1}.
 //
-// GPU mapping: a stage-level kernel (Sec. 4.1.2): each tree node is done on
-// chip, so the 2 ell digit polynomials never leave the SMs. A node is one
-// thread-block cluster of 2L CTAs of ntt::HALF threads, CTA (p, l) working on
-// input polynomial p and limb l: the two polynomials go through separate
-// inverse NTTs, Dcps and forward NTTs and meet only in the final sum, so the
-// split doubles the parallelism of every stage (the late stages have few
-// nodes) without repeating any transform. Thread b owns slots / coefficients
-// b + (N/8) e (see ntt.cuh). The exchanges go through distributed shared
-// memory: the CRT of the Dcp reads the other limb's residues, and the
-// polynomial-1 CTA hands its reduced partial sums to the polynomial-0 CTA.
-// Shared memory per CTA: the limb's coefficients of its polynomial (padded),
-// the Dcp offset values y = x + O of the owned coefficients (one CRT per
-// coefficient, after which each digit is a shift and a mask, see ntt.cuh),
-// and two work buffers for the digit transforms, used in turn so that one
-// digit's last round and the next digit's first round need no barrier between
-// them. About 81 KB at N = 4096, so two CTAs share an SM and their phases
+// GPU mapping: stage-level kernels (Sec. 4.1.2): each tree node is done on
+// chip, so the 2 ell digit polynomials never leave the SMs; one launch per
+// stage. Thread b of a CTA (ntt::HALF threads, one limb) owns slots /
+// coefficients b + (N/8) e (see ntt.cuh). Two cluster shapes, chosen per stage
+// (Sec. 4.4):
+//   - coltor_limb_kernel: one cluster of L CTAs per node, CTA l on limb l for
+//     both input polynomials (2 inverse NTTs sharing their rounds, then the
+//     2 ell digit transforms); used while the nodes fill the GPU;
+//   - coltor_split_kernel: one cluster of 2L CTAs per node, CTA (p, l) on
+//     polynomial p and limb l: the two polynomials go through separate inverse
+//     NTTs, Dcps and forward NTTs and meet only in the final sum, so the split
+//     doubles the parallelism of a stage without repeating any transform; used
+//     for the late stages with few nodes.
+// The exchanges go through distributed shared memory: the CRT of the Dcp reads
+// the other limb's residues, and (split kernel) the polynomial-1 CTA hands its
+// reduced partial sums to the polynomial-0 CTA. Shared memory per CTA: the
+// limb's coefficients (padded), the Dcp offset values y = x + O of the owned
+// coefficients of the current polynomial (one CRT per coefficient, after which
+// each digit is a shift and a mask, see ntt.cuh), and two work buffers for the
+// digit transforms, used in turn so that one digit's last round and the next
+// digit's first round need no barrier between them: 98.8 KB (limb kernel) or
+// 82.3 KB (split kernel) at N = 4096, two CTAs per SM, so that their phases
 // (transform-bound, load-bound) overlap. The multiply-accumulate keeps 64-bit
-// sums in
-// registers: each of the ell terms is below 4q * q < 2^58, so the sum stays
-// below 2^60 and one Barrett reduction per output finishes it.
+// sums in registers: each of the at most 2 ell terms is below 4q * q < 2^58,
+// so the sum stays below 2^61 and one Barrett reduction per output finishes it.
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -187,8 +192,8 @@ __global__ void __launch_bounds__(ntt::HALF, 2) coltor_split_kernel(const __grid
   const Limb &T = R.limb[h];
   const uint32_t q = T.q;
   uint32_t *res = sm;                                             // [PN]: coefficients of polynomial pp, limb h
-  int64_t *ybuf = reinterpret_cast<int64_t *>(sm + PN + (PN & 1)); // [N]: Dcp offset values
-  uint32_t *work = sm + PN + (PN & 1) + 2 * N;                    // [2][PN]: two digit buffers, then partial sums
+  int64_t *ybuf = reinterpret_cast<int64_t *>(sm + PN + (PN & 1)); // [N]: Dcp offset values, then partial sums
+  uint32_t *work = sm + PN + (PN & 1) + 2 * N;                    // [2][PN]: two digit buffers
 
   const uint32_t node = blockIdx.x / (2 * L);
   const uint32_t c = node / p.nodes_per_client, k = node % p.nodes_per_client;

@@ -17,13 +17,18 @@
 // tau_k(b) while it loads them. The slot values of X^(-2^j) are
 // psi^-((2s+1) 2^j mod 2N), read from a table.
 //
-// GPU mapping: a stage-level kernel (Sec. 4.1.2), one thread-block cluster of
-// L CTAs per tree node, CTA l on limb l, the CRT of the Dcp reading the other
-// limb's residues through distributed shared memory (see ntt.cuh and
-// coltor.cu); about 81 KB of shared memory per CTA at N = 4096. The tree
-// runs in place in the output array: stage j reads list[k], k < 2^j, and
-// writes list[k] and list[k + 2^j]; list[k] is read by its own CTA only, and
-// every read of it comes before the barrier that precedes the writes. Only
+// GPU mapping: stage-level kernels (Sec. 4.1.2), one launch per stage, the
+// cluster shape chosen per stage (Sec. 4.4):
+//   - expand_stage_kernel: one thread-block cluster of L CTAs per tree node,
+//     CTA l on limb l, the CRT of the Dcp reading the other limb's residues
+//     through distributed shared memory (see ntt.cuh and coltor.cu); about
+//     81 KB of shared memory per CTA at N = 4096;
+//   - expand_split_kernel: for stages with few nodes, L ell CTAs per node
+//     (limb x digit), each repeating the inverse NTT and doing one digit.
+// The tree runs in place in the output array: stage j reads list[k], k < 2^j,
+// and writes list[k] and list[k + 2^j]; each CTA reads only its limb of
+// list[k], and every such read comes before the barrier that precedes the
+// writes of that limb. Only
 // the outputs with index < n_out are computed at any stage (an intermediate
 // list[k] feeds final outputs k, k + 2^(j+1), ..., so k < n_out is exactly the
 // condition for it to be needed).
