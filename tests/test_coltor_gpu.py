@@ -156,3 +156,28 @@ def test_coltor_argument_errors(g):
         assert g.lib.gpir_coltor(p3, 1, 2, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), None) == g.GPIR_ENOTSUP
     finally:
         g.gpir_params_destroy(p3)
+
+
+def test_coltor_bench_configuration_decrypts(g):
+    """The bench's ColTor configuration exactly (32 clients x 64 ciphertexts,
+    N = 4096, 2 limbs: limb kernel for stages 0-3, split kernel for 4-5), with
+    noiseless toy inputs: every client decrypts to its selected record."""
+    N, L, D1, B = 4096, 2, 64, 32
+    primes = P28
+    ell = oracle.gadget_digits(primes)
+    cts, rgsws, secrets, recs, picks = [], [], [], [], []
+    for c in range(B):
+        js = (c * 37 + 5) % D1
+        ct, rgsw, s, rec = synth.toy_coltor_inputs(1000 + c, D1, L, N, primes, js, ell)
+        cts.append(ct)
+        rgsws.append(rgsw)
+        secrets.append(s)
+        recs.append(rec)
+        picks.append(js)
+    got = _gpu_coltor(g, primes, N, np.stack(cts), np.stack(rgsws))
+    for c in range(B):
+        for l, q in enumerate(primes):
+            a = got[c, 0, l].astype(np.uint64)
+            b = got[c, 1, l].astype(np.uint64)
+            m = (b + np.uint64(q) - (a * secrets[c][l].astype(np.uint64)) % np.uint64(q)) % np.uint64(q)
+            assert np.array_equal(m, recs[c][picks[c]][l].astype(np.uint64)), "client %d limb %d" % (c, l)

@@ -105,6 +105,36 @@ def test_expand_toy_decrypts_to_scaled_message_full_ring(g, L):
             assert np.array_equal(ph, np.repeat(want[:, None], N, axis=1)), "client %d limb %d" % (c, l)
 
 
+def test_expand_bench_configuration_decrypts(g):
+    """The bench's ExpandQuery configuration exactly (32 clients, J = 9 stages,
+    ragged n_out = 274, N = 4096, 2 limbs), with noiseless toy inputs whose
+    messages have coefficients below 2^J: output r of each client decrypts to
+    the constant 2^J m_r."""
+    N, L, J, n_out, B = 4096, 2, 9, 274, 32
+    primes = P28
+    ell = oracle.gadget_digits(primes)
+    psis = [oracle.psi_2n(q, N) for q in primes]
+    queries, evks, secrets, msgs = [], [], [], []
+    for c in range(B):
+        q_, evk, s, m = eu.toy_expand_inputs(2000 + c, J, L, N, primes, ell)
+        m = [x if i < n_out else 0 for i, x in enumerate(m)]
+        for l, q in enumerate(primes):
+            M = oracle.ntt_negacyclic([x % q for x in m], q, psis[l])
+            q_[1, l] = ((q_[0, l].astype(np.uint64) * s[l].astype(np.uint64) + M) % np.uint64(q)).astype(np.uint32)
+        queries.append(q_)
+        evks.append(evk)
+        secrets.append(s)
+        msgs.append(m)
+    got = _gpu_expand(g, primes, N, np.stack(queries), np.stack(evks), n_out)
+    for c in range(B):
+        for l, q in enumerate(primes):
+            a = got[c, :, 0, l].astype(np.uint64)
+            b = got[c, :, 1, l].astype(np.uint64)
+            ph = (b + np.uint64(q) - (a * secrets[c][l].astype(np.uint64)[None, :]) % np.uint64(q)) % np.uint64(q)
+            want = np.array([((1 << J) * msgs[c][r]) % q for r in range(n_out)], dtype=np.uint64)
+            assert np.array_equal(ph, np.repeat(want[:, None], N, axis=1)), "client %d limb %d" % (c, l)
+
+
 def test_expand_rowsel_coltor_returns_scaled_db_entry(g):
     """The three server phases chained on the GPU at N = 4096: a toy query
     encrypting X^(i*) expands into a one-hot selection vector (scaled by 2^J),
