@@ -304,7 +304,9 @@ int gpir_expand_query(const gpir_params_t *params, uint32_t batch, uint32_t stag
  *   out_dev   device, [B][2][L][N]
  * No buffer may overlap another. Each phase's limits and workspaces are those
  * of its own call; the first error is returned and later phases are not
- * enqueued. Asynchronous. */
+ * enqueued. After one call with the same shapes on the same stream (tables,
+ * workspaces and kernel attributes then exist), the call allocates nothing and
+ * can be captured into a CUDA graph. Asynchronous. */
 int gpir_pir_batch(const gpir_db_t *db, uint32_t batch, uint32_t stages, const uint32_t *query_dev,
                    const uint32_t *evk_dev, const uint32_t *rgsw_dev, uint32_t *sel_dev, uint32_t *rows_dev,
                    uint32_t *out_dev, int path, void *stream);

@@ -259,3 +259,40 @@ def test_pir_batch_equals_the_three_calls_and_decrypts(g):
             b = want[c, 1, l].astype(np.uint64)
             m = (b + np.uint64(q) - (a * secrets[c][l].astype(np.uint64)) % np.uint64(q)) % np.uint64(q)
             assert np.array_equal(m, (db[i, j, l].astype(np.uint64) * np.uint64(1 << J)) % np.uint64(q))
+
+
+def test_pir_batch_replays_from_a_cuda_graph(g):
+    """After one warm-up call (tables, workspaces and kernel attributes exist),
+    gpir_pir_batch can be captured into a CUDA graph; replays give the result
+    of a direct call."""
+    import torch
+    from tests.gpu_util import DbHandle, to_dev
+    N, L, D0, D1, J, B = 512, 2, 32, 8, 5, 3
+    primes = P28
+    ell = oracle.gadget_digits(primes)
+    db = synth.uniform_residues(931, synth.TAG_DB, (D0, D1, L, N), primes, limb_axis=2)
+    h = DbHandle(g, db, N, primes, path_mask=g.GPIR_PATH_TC)
+    try:
+        query = to_dev(synth.uniform_residues(932, eu.TAG_QUERY, (B, 2, L, N), primes, limb_axis=2))
+        evk = to_dev(synth.uniform_residues(933, eu.TAG_EVK, (B, J, ell, 2, L, N), primes, limb_axis=4))
+        rgsw = to_dev(synth.uniform_residues(934, synth.TAG_RGSW, (B, 3, 2 * ell, 2, L, N), primes, limb_axis=4))
+        sel = torch.empty((B, D0, 2, L, N), dtype=torch.int32, device="cuda")
+        rows = torch.empty((B, D1, 2, L, N), dtype=torch.int32, device="cuda")
+        want = torch.empty((B, 2, L, N), dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            g.gpir_pir_batch(h.h, B, J, query, evk, rgsw, sel, rows, want, g.GPIR_PATH_TC, s)   # warm-up
+        s.synchronize()
+        out = torch.full((B, 2, L, N), -1, dtype=torch.int32, device="cuda")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            g.gpir_pir_batch(h.h, B, J, query, evk, rgsw, sel, rows, out, g.GPIR_PATH_TC,
+                             torch.cuda.current_stream())
+        for _ in range(2):
+            out.fill_(-1)
+            graph.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, want)
+        g.gpir_sync(None, 20000)
+    finally:
+        h.close()
