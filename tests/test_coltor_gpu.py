@@ -181,3 +181,18 @@ def test_coltor_bench_configuration_decrypts(g):
             b = got[c, 1, l].astype(np.uint64)
             m = (b + np.uint64(q) - (a * secrets[c][l].astype(np.uint64)) % np.uint64(q)) % np.uint64(q)
             assert np.array_equal(m, recs[c][picks[c]][l].astype(np.uint64)), "client %d limb %d" % (c, l)
+
+
+def test_coltor_zero_inputs_give_zero(g):
+    """All-zero ciphertexts (and RGSW rows) give an all-zero result; all-zero
+    differences with random RGSW rows give back ct_0 exactly."""
+    primes = P28
+    B, D1, L, N = 2, 8, 2, 256
+    ell = oracle.gadget_digits(primes)
+    ct = np.zeros((B, D1, 2, L, N), dtype=np.uint32)
+    rgsw = synth.uniform_residues(951, synth.TAG_RGSW, (B, 3, 2 * ell, 2, L, N), primes, limb_axis=4)
+    assert not _gpu_coltor(g, primes, N, ct, np.zeros_like(rgsw)).any()
+    same = synth.uniform_residues(952, synth.TAG_COLTOR, (B, 1, 2, L, N), primes, limb_axis=3)
+    ct = np.repeat(same, D1, axis=1)                     # every pair differs by zero
+    got = _gpu_coltor(g, primes, N, ct, rgsw)
+    assert np.array_equal(got, same[:, 0])

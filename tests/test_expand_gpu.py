@@ -296,3 +296,19 @@ def test_pir_batch_replays_from_a_cuda_graph(g):
         g.gpir_sync(None, 20000)
     finally:
         h.close()
+
+
+def test_expand_degenerate_cases(g):
+    """n_out = 1 with J = 3 (every stage computes only index 0, no X^(-2^j)
+    output) against the oracle; an all-zero query and keys expand to zeros."""
+    primes = P28
+    N, L, J = 256, 2, 3
+    ell = oracle.gadget_digits(primes)
+    query = synth.uniform_residues(941, eu.TAG_QUERY, (2, 2, L, N), primes, limb_axis=2)
+    evk = synth.uniform_residues(942, eu.TAG_EVK, (2, J, ell, 2, L, N), primes, limb_axis=4)
+    got = _gpu_expand(g, primes, N, query, evk, 1)
+    for c in range(2):
+        assert np.array_equal(got[c], oracle.expand_query(query[c], evk[c], primes, 1))
+    zq = np.zeros_like(query)
+    ze = np.zeros_like(evk)
+    assert not _gpu_expand(g, primes, N, zq, ze, 8).any()
