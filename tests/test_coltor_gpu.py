@@ -49,6 +49,8 @@ SHAPES = [
     (1, 2, 2, 4096),           # the workload ring size
     (10, 64, 2, 32),           # >= 2 CTAs per SM of nodes: the limb kernel in the early stages, the split one late
     (10, 64, 1, 32),           # the same with one limb
+    (2, 4, 1, 256),            # logn = 8: a radix-4 middle round
+    (1, 4, 2, 2048),           # logn = 11: radix-8 + radix-4 middle rounds
 ]
 
 

@@ -50,6 +50,9 @@ SHAPES = [
     (1, 2, 4, 2, 4096),         # the workload ring size
     (20, 5, 32, 2, 32),         # >= 2 CTAs per SM of nodes in the last stage: the limb kernel there, the split one before
     (20, 5, 29, 1, 32),         # the same with one limb, ragged
+    (1, 4, 16, 1, 256),         # logn = 8: a radix-4 middle round
+    (2, 3, 8, 2, 1024),         # logn = 10: two radix-4 middle rounds
+    (2, 3, 7, 2, 2048),         # logn = 11: radix-8 + radix-4 middle rounds
 ]
 
 
