@@ -1,0 +1,123 @@
+"""A CPU model of the tensor-core RowSel arithmetic, checked against the oracle.
+
+The tensor-core path (tcgen05 .kind::f16) rests on an exactness argument:
+  - each residue x < 2^28 splits into balanced base-256 digits, byte u of
+    x + 0x808080 minus 128 for u < 3 and byte 3 as is, so that
+    x = sum_u d_u 2^(8u) with d_0..d_2 in [-128, 127] and d_3 in [0, 16],
+    every digit exactly an fp16;
+  - a digit product is at most 2^14 in magnitude, so a sum over a group of
+    512 rows is at most 2^23 and every partial sum is an integer an fp32
+    accumulator holds exactly, in any order;
+  - the group sums D_uv are recombined as sum_uv D_uv (2^(8(u+v)) mod q) in
+    64-bit integers (< 2^55 per group), up to 8 groups are added (< 2^58), and
+    one Barrett reduction of the sum plus off58 (the smallest multiple of q not
+    below 2^58) finishes each flush.
+This model restates those steps with numpy (float32 group products, int64
+recombination) without any code of the CUDA path, and checks the result
+against the oracle; a negative control shows the float32 sums failing once the
+group bound is broken.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+PRIMES = synth.PRIMES_28
+GROUP = 512
+FLUSH = 8
+
+
+def digits(x):
+    """[..., 4] balanced base-256 digits of x (uint32 array, x < 2^28)."""
+    xp = x.astype(np.int64) + 0x808080
+    d = np.stack([(xp >> (8 * u)) & 0xFF for u in range(4)], axis=-1)
+    d[..., :3] -= 128
+    return d
+
+
+def tc_model_rowsel(ct, db, primes):
+    """ct [B][D0][2][L][T], db [D0][D1][L][T] -> [B][D1][2][L][T] through the digit model."""
+    ct = np.asarray(ct)
+    db = np.asarray(db)
+    B, D0, _, L, T = ct.shape
+    D1 = db.shape[1]
+    out = np.zeros((B, D1, 2, L, T), dtype=np.uint64)
+    for l, q in enumerate(primes):
+        q = int(q)
+        c = np.array([pow(2, 8 * s, q) for s in range(7)], dtype=np.int64)
+        off58 = -(-(1 << 58) // q) * q
+        for t in range(T):
+            a = digits(ct[:, :, :, l, t].transpose(0, 2, 1).reshape(2 * B, D0))     # [2B][D0][4]
+            bd = digits(db[:, :, l, t])                                               # [D0][D1][4]
+            res = np.zeros((2 * B, D1), dtype=np.uint64)
+            acc = np.zeros((2 * B, D1), dtype=np.int64)
+            groups = 0
+            for g0 in range(0, D0, GROUP):
+                g1 = min(D0, g0 + GROUP)
+                for u in range(4):
+                    A = a[:, g0:g1, u].astype(np.float32)
+                    for v in range(4):
+                        Bm = bd[g0:g1, :, v].astype(np.float32)
+                        D = (A @ Bm).astype(np.float64)               # fp32 products and sums
+                        assert np.all(np.abs(D) <= 2 ** 23)
+                        acc += np.rint(D).astype(np.int64) * c[u + v]
+                groups += 1
+                if groups == FLUSH or g1 == D0:
+                    assert np.all(np.abs(acc) < 2 ** 58)
+                    r = ((acc + off58).astype(np.uint64) % np.uint64(q))
+                    res = (res + r) % np.uint64(q)
+                    acc[:] = 0
+                    groups = 0
+            out[:, :, :, l, t] = res.reshape(B, 2, D1).transpose(0, 2, 1)
+    return out.astype(np.uint32)
+
+
+def test_digit_split_reconstructs_and_fits_fp16():
+    rng = np.random.default_rng(1)
+    for q in PRIMES:
+        xs = np.concatenate([rng.integers(0, q, 20000), [0, 1, 127, 128, 255, 256, 0x7F7F7F, 0x808080, q - 1,
+                                                         (1 << 28) - 1]]).astype(np.uint32)
+        d = digits(xs)
+        assert np.array_equal((d * (256 ** np.arange(4))).sum(axis=-1), xs.astype(np.int64))
+        assert d[..., :3].min() >= -128 and d[..., :3].max() <= 127
+        assert d[..., 3].min() >= 0 and d[..., 3].max() <= 16
+        assert np.array_equal(d.astype(np.float16).astype(np.int64), d)      # exact fp16 values
+
+
+def test_group_sums_are_exact_in_fp32_at_the_bound():
+    """The worst case of a 512-row group (all digit products 2^14) and random
+    signed digits: float32 sums equal the integer sums."""
+    a = np.full((4, GROUP), -128, dtype=np.int64)
+    b = np.full((GROUP, 4), -128, dtype=np.int64)
+    assert np.array_equal((a.astype(np.float32) @ b.astype(np.float32)).astype(np.int64), a @ b)
+    rng = np.random.default_rng(2)
+    a = rng.integers(-128, 128, (64, GROUP))
+    b = rng.integers(-128, 128, (GROUP, 64))
+    assert np.array_equal((a.astype(np.float32) @ b.astype(np.float32)).astype(np.int64), a @ b)
+
+
+def test_group_bound_is_needed():
+    """Negative control: over 8 x 512 rows of odd products a float32 running sum
+    passes 2^24 and drops low bits."""
+    a = np.full(8 * GROUP, 127, dtype=np.int64)
+    b = np.full(8 * GROUP, 127, dtype=np.int64)
+    acc = np.float32(0)
+    for x, y in zip(a, b):
+        acc = np.float32(acc + np.float32(x * y))
+    assert int(acc) != int((a * b).sum())
+
+
+@pytest.mark.parametrize("shape", [(2, 5000, 7, 2, 3), (1, 513, 4, 1, 2), (3, 64, 5, 2, 4)])
+def test_model_equals_oracle(shape):
+    """Random residues and the all-(q-1) worst case, D0 across several groups and flushes."""
+    B, D0, D1, L, T = shape
+    primes = PRIMES[:L]
+    ct = synth.uniform_residues(61 + D0, synth.TAG_CT, (B, D0, 2, L, T), primes, limb_axis=3)
+    db = synth.uniform_residues(62 + D0, synth.TAG_DB, (D0, D1, L, T), primes, limb_axis=2)
+    assert np.array_equal(tc_model_rowsel(ct, db, primes), oracle.rowsel(ct, db, primes))
+    qm = np.array(primes, dtype=np.uint32)
+    ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
+    db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
+    assert np.array_equal(tc_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
