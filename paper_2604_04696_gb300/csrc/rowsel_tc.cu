@@ -163,6 +163,99 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_peer(uint32_t local_saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_saddr), "r"(rank));
+  return r;
+}
+// Arrive on barrier `bar` (same offset) in every CTA of `mask` once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_cluster(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+
+// ---- SM-pair (cta_group::2) wrappers -----------------------------------------
+//
+// kind::f16 across the two CTAs of a cluster pair: M = 256 (each CTA supplies
+// 128 rows of A from its own shared memory and receives them in its own
+// tensor memory), N = 256 (each CTA supplies half of the B rows, at the same
+// shared-memory offset), K = 16. Issued by one thread of the even CTA.
+constexpr uint32_t kIdescPair = (1u << 4) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on barrier `bar` (same offset) in both CTAs of the pair once the
+// pair MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+// Arrive (release, cluster scope) on a barrier of another CTA of the cluster,
+// given its shared::cluster address.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// Relaxed arrive on a barrier of another CTA of the cluster: a signal that
+// carries no data of this thread (a cluster-scope release would first wait
+// for this SM's outstanding global stores, microseconds under the ingest's
+// ring traffic).
+__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// try_wait with cluster-scope acquire: sees what a peer CTA wrote before its
+// release arrive on this barrier.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void st_cluster_u64(uint32_t cluster_addr, uint64_t v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -555,6 +648,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 // number of CTAs is resident. Counters are monotonic and zeroed before the
 // launch. Unit ids travel producer -> MMA thread -> epilogue through shared
 // memory with the stage and accumulator barriers. All waits are bounded.
+//
+// SM-pair form (PAIR = true, clusters of 2 CTAs, cta_group::2). A pair unit
+// (E2, slot, n-block) covers the two m-blocks of entries 2 E2 (even CTA) and
+// 2 E2 + 1 (odd CTA) against ONE database tile: each CTA bulk-copies its own
+// A tile (16 KB per k-chunk) and half of the B tile (16 KB, B rows 128 r ..
+// 128 r + 127 for CTA rank r), and the even CTA's MMA thread issues M = 256,
+// N = 256 MMAs that read both CTAs' shared memory and write both CTAs' tensor
+// memory. Per SM that is 32 KB of operands per k-chunk instead of 48 KB, for
+// the same tensor work. Protocol on top of the single-CTA form:
+//   - the even CTA's producer claims units and hands each to the odd CTA's
+//     producer through a 4-slot mailbox (remote store + release arrive);
+//   - the odd CTA's warp 1 relays "my operands of stage st have landed" to the
+//     even CTA's pfull[st];
+//   - MMA commits arrive on empty[st] and acc_full[b] in both CTAs
+//     (multicast), and the odd CTA's epilogue warps also arrive on the even
+//     CTA's acc_empty[b] (count 16 there);
+//   - each CTA's epilogue, store warp and ring accounting work on its own
+//     entry 2 E2 + rank, exactly as in the single-CTA form.
+// Both CTAs walk the same unit sequence, so their stage and accumulator
+// phases stay aligned. The lookahead compares entries with claimed pair
+// units (two entries each), and the deadlock argument carries over: the
+// smallest unfinished pair unit depends only on ring entries R back and on
+// claims already made. Needs an even number of m-blocks.
 
 constexpr int F_EPI_WARPS = 8;
 // Exact fp32 group of the fused kernel: 512 rows, so |D| <= 512 * 2^14 = 2^23,
@@ -572,6 +688,11 @@ constexpr int F_RAW_BYTES = 16 * KCHUNK * 2 * 8 * 4;           // raw box: 16 cl
 constexpr int F_OUT_BYTES = MROWS * NCOLS * 4;                 // one unit's 32 x 64 output block
 constexpr size_t FUSED_SMEM = 1024 + (size_t)FSTAGES * STAGE_BYTES + F_RAW_BYTES + F_OUT_BYTES + 256;
 static_assert(FUSED_SMEM <= 232448, "fused kernel shared memory exceeds 227 KB");
+constexpr int P_STAGES = 4;                                    // pair form: operand stages (32 KB each)
+constexpr int P_STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES / 2;
+constexpr int P_MAIL = 4;                                      // pair form: claimed units in flight to the odd CTA
+constexpr size_t PAIR_SMEM = 1024 + (size_t)P_STAGES * P_STAGE_BYTES + F_RAW_BYTES + F_OUT_BYTES + 512;
+static_assert(PAIR_SMEM <= 232448, "pair kernel shared memory exceeds 227 KB");
 
 constexpr uint64_t kNoUnit = ~0ull;
 
@@ -646,36 +767,50 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
 }
 
-template <bool PROF>
+template <bool PROF, bool PAIR>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
+  constexpr int NST = PAIR ? P_STAGES : FSTAGES;
+  constexpr int SBYTES = PAIR ? P_STAGE_BYTES : STAGE_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *rawbuf = smem + FSTAGES * STAGE_BYTES;
+  uint8_t *rawbuf = smem + NST * SBYTES;
   uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbuf + F_RAW_BYTES);   // [32 m][64 n], swizzled
   uint64_t *full = reinterpret_cast<uint64_t *>(rawbuf + F_RAW_BYTES + F_OUT_BYTES);
-  uint64_t *empty = full + FSTAGES;
-  uint64_t *acc_full = empty + FSTAGES;
+  uint64_t *empty = full + NST;
+  uint64_t *acc_full = empty + NST;
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *raw_bar = acc_empty + 2;
-  uint64_t *stage_unit = raw_bar + 1;                 // [FSTAGES]
-  uint64_t *acc_unit = stage_unit + FSTAGES;          // [2]
+  uint64_t *stage_unit = raw_bar + 1;                 // [NST]
+  uint64_t *acc_unit = stage_unit + NST;              // [2]
   uint64_t *task_slot = acc_unit + 2;                 // claimed ingest task
   uint64_t *ostage_full = task_slot + 1;              // out_stage holds a unit's block
   uint64_t *ostage_empty = ostage_full + 1;           // the store warp has drained it
   uint64_t *ostage_unit = ostage_empty + 1;           // whose block (or kNoUnit)
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ostage_unit + 1);
+  uint64_t *pfull = ostage_unit + 1;                  // pair: [NST] the odd CTA's operands have landed
+  uint64_t *mail = pfull + (PAIR ? NST : 0);          // pair: [P_MAIL] claimed units, even -> odd CTA
+  uint64_t *mail_full = mail + (PAIR ? P_MAIL : 0);
+  uint64_t *mail_empty = mail_full + (PAIR ? P_MAIL : 0);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail_empty + (PAIR ? P_MAIL : 0));
   volatile uint32_t *abort_flag = tmem_slot + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < FSTAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      if (PAIR) mbar_init(&pfull[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 2);      // the MMA commit + the MMA thread's arrive after writing acc_unit
-      mbar_init(&acc_empty[b], F_EPI_WARPS);
+      // pair: the even CTA's MMAs wait for both CTAs' epilogues
+      mbar_init(&acc_empty[b], (PAIR && rank == 0) ? 2 * F_EPI_WARPS : F_EPI_WARPS);
     }
+    if (PAIR)
+      for (int i = 0; i < P_MAIL; ++i) {
+        mbar_init(&mail_full[i], 1);
+        mbar_init(&mail_empty[i], 1);
+      }
     mbar_init(raw_bar, 1);
     mbar_init(ostage_full, F_EPI_WARPS);
     mbar_init(ostage_empty, 1);
@@ -683,21 +818,38 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     fence_mbar_init();
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates the same columns in both
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR)
+    cluster_sync_all();   // both CTAs' barriers and tensor memory exist before either uses the other's
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  auto try_wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    if constexpr (PAIR)
+      return mbar_try_wait_cluster(bar, parity);
+    else
+      return mbar_try_wait(bar, parity);
+  };
   auto wait = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (try_wait(bar, parity)) return true;
     uint64_t t0 = globaltimer_ns();
     for (uint32_t n = 1;; ++n) {
-      if (mbar_try_wait(bar, parity)) return true;
+      if (try_wait(bar, parity)) return true;
       if ((n & 63u) == 0) {
         if (*abort_flag) return false;
         if (globaltimer_ns() - t0 > kWaitLimitNs) {
@@ -766,10 +918,30 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       uint32_t st = 0, ph = 0;
       bool ok = true;
       const uint64_t pol_first = l2_policy_evict_first();
+      constexpr uint32_t B_BYTES = PAIR ? B_TILE_BYTES / 2 : B_TILE_BYTES;   // pair: this CTA's half of B
+      uint32_t mi = 0;                                                      // pair: mailbox sequence number
       for (;;) {
-        const uint64_t u = atomicAdd(&p.ctr[0], 1ull);
-        if (u >= p.n_units) break;
-        const uint64_t E = u / p.upe;
+        uint64_t u;
+        if constexpr (PAIR) {
+          const uint32_t ms = mi % P_MAIL, mph = (mi / P_MAIL) & 1u;
+          ++mi;
+          if (rank == 0) {
+            u = atomicAdd(&p.ctr[0], 1ull);
+            if (u >= p.n_units) u = kNoUnit;
+            if (!(ok = wait(&mail_empty[ms], mph ^ 1u, kErrQueueWait))) break;
+            st_cluster_u64(map_peer(smem_u32(&mail[ms]), 1), u);
+            mbar_arrive_remote(map_peer(smem_u32(&mail_full[ms]), 1));
+          } else {
+            if (!(ok = wait(&mail_full[ms], mph, kErrQueueWait))) break;
+            u = *reinterpret_cast<volatile uint64_t *>(&mail[ms]);
+            mbar_arrive_remote(map_peer(smem_u32(&mail_empty[ms]), 0));
+          }
+          if (u == kNoUnit) break;
+        } else {
+          u = atomicAdd(&p.ctr[0], 1ull);
+          if (u >= p.n_units) break;
+        }
+        const uint64_t E = PAIR ? (u / p.upe) * 2 + rank : u / p.upe;
         const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
         const uint32_t g = (uint32_t)(E / p.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
@@ -777,18 +949,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
                                wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
         fence_proxy_async_global();
         const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)A_TILE_BYTES;
-        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES;
+        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)B_TILE_BYTES +
+                               (PAIR ? rank * (uint64_t)B_BYTES : 0ull);
         for (uint32_t kc = 0; kc < p.kch; ++kc) {
           if (!(ok = FUSED_TIMED(kPWaitEmpty, wait(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
           stage_unit[st] = u;   // read by the MMA thread on the unit's first stage
-          uint8_t *sa = smem + st * STAGE_BYTES;
-          mbar_arrive_expect_tx(&full[st], STAGE_BYTES);
+          uint8_t *sa = smem + st * SBYTES;
+          mbar_arrive_expect_tx(&full[st], SBYTES);
           bulk_g2s(sa, a_src + (uint64_t)kc * A_TILE_BYTES, A_TILE_BYTES, &full[st]);
           if (p.hints & kHintDbEvictFirst)
-            bulk_g2s_hint(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st], pol_first);
+            bulk_g2s_hint(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_BYTES, &full[st], pol_first);
           else
-            bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_TILE_BYTES, &full[st]);
-          if (++st == FSTAGES) {
+            bulk_g2s(sa + A_TILE_BYTES, b_src + (uint64_t)kc * B_TILE_BYTES, B_BYTES, &full[st]);
+          if (++st == NST) {
             st = 0;
             ph ^= 1u;
           }
@@ -799,8 +972,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       if (ok && wait(&empty[st], ph ^ 1u, kErrTmaWait)) {
         stage_unit[st] = kNoUnit;
         mbar_arrive(&full[st]);
+        if constexpr (PAIR) {
+          // the last multicast commits target this CTA's empty barriers too:
+          // let them land before the CTA can leave
+          for (int s2 = 1; s2 < NST; ++s2) {
+            if (++st == NST) {
+              st = 0;
+              ph ^= 1u;
+            }
+            mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
+          }
+        }
       } else {
-        for (int s2 = 0; s2 < FSTAGES; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
+        for (int s2 = 0; s2 < NST; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
       }
     }
   } else if (warp == 1) {
@@ -831,21 +1015,47 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
           for (uint32_t kc = c0; kc < c1; ++kc) {
             if (!first && !(ok = FUSED_TIMED(kMWaitFull, wait(&full[st], ph, kErrTmaWait)))) break;
             first = false;
+            if constexpr (PAIR) {
+              if (rank != 0) {
+                // odd CTA: its operands of stage st have landed (the bulk copies
+                // completed before full[st] did); tell the issuer
+                mbar_arrive_remote_relaxed(map_peer(smem_u32(&pfull[st]), 0));
+                if (++st == NST) {
+                  st = 0;
+                  ph ^= 1u;
+                }
+                continue;
+              }
+              if (!(ok = FUSED_TIMED(kMWaitFull, wait(&pfull[st], ph, kErrTmaWait)))) break;
+            }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + st * STAGE_BYTES);
+            const uint32_t sa = smem_u32(smem + st * SBYTES);
             const uint32_t sb = sa + A_TILE_BYTES;
 #pragma unroll
-            for (int k16 = 0; k16 < KCHUNK / 16; ++k16)
-              mma_f16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32), (kc > c0 || k16 > 0) ? 1u : 0u);
-            mma_commit(&empty[st]);
-            if (++st == FSTAGES) {
+            for (int k16 = 0; k16 < KCHUNK / 16; ++k16) {
+              if constexpr (PAIR)
+                mma_f16_pair(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32),
+                             (kc > c0 || k16 > 0) ? 1u : 0u);
+              else
+                mma_f16(tmem_d, sw128_desc(sa + k16 * 32), sw128_desc(sb + k16 * 32),
+                        (kc > c0 || k16 > 0) ? 1u : 0u);
+            }
+            if constexpr (PAIR)
+              mma_commit_pair(&empty[st]);
+            else
+              mma_commit(&empty[st]);
+            if (++st == NST) {
               st = 0;
               ph ^= 1u;
             }
           }
           if (!ok) break;
           acc_unit[buf] = u | ((gi + 1 == kgroups) ? (1ull << 63) : 0ull);   // unit id, top bit: last group
-          mma_commit(&acc_full[buf]);
+          if constexpr (PAIR) {
+            if (rank == 0) mma_commit_pair(&acc_full[buf]);   // the odd CTA gets this commit too
+          } else {
+            mma_commit(&acc_full[buf]);
+          }
           mbar_arrive(&acc_full[buf]);
           aph[buf] ^= 1u;
           buf ^= 1u;
@@ -905,7 +1115,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       }
       const uint64_t un = tag & ~(1ull << 63);
       const bool last = (tag >> 63) != 0;
-      const uint64_t E = un / p.upe;
+      const uint64_t E = PAIR ? (un / p.upe) * 2 + rank : un / p.upe;   // this CTA's entry
       const uint32_t l = (uint32_t)(E / p.mblk) / p.gpl;
       const TcLimb &lm = p.limb[l];
       if (last && signaller) atomicAdd(&p.consumed[E % p.R], 1u);   // its ring tiles are no longer needed
@@ -939,7 +1149,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      if (lane == 0) {
+        mbar_arrive(&acc_empty[buf]);
+        // the issuer's count; the tensor-memory loads above have completed
+        if (PAIR && rank != 0) mbar_arrive_remote_relaxed(map_peer(smem_u32(&acc_empty[buf]), 0));
+      }
       aph[buf] ^= 1u;
       buf ^= 1u;
       if (last || ++ngroups == F_FLUSH_GROUPS) {
@@ -984,7 +1198,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
       if (!okw) break;
       const uint64_t un = *ostage_unit;
       if (un == kNoUnit) break;
-      const uint64_t E = un / p.upe;
+      const uint64_t E = PAIR ? (un / p.upe) * 2 + rank : un / p.upe;
       const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
       const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
       const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
@@ -1043,7 +1257,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
         // ingest stays within `lookahead` entries of the GEMM units' claims
         // (so that ring lines are read back while still in L2)
         const bool near = p.lookahead == 0 || E < p.lookahead ||
-                          FUSED_TIMED(kIWaitConsumed, wait_claims((E - p.lookahead) * p.upe));
+                          FUSED_TIMED(kIWaitConsumed, wait_claims(((E - p.lookahead) >> (PAIR ? 1 : 0)) * p.upe));
         if (near && (E < p.R || FUSED_TIMED(kIWaitConsumed,
                                             wait_count(&p.consumed[E % p.R], (uint32_t)((E / p.R) * p.upe))))) {
           mbar_arrive_expect_tx(raw_bar, F_RAW_BYTES);
@@ -1125,10 +1339,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid
     if (threadIdx.x == 0) atomicAdd(&p.prof[kCtaCycles], clock64() - kstart);
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR)
+    cluster_sync_all();   // no peer still reads this CTA's memory or arrives on its barriers
+  else
+    __syncthreads();
   tc_fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  if (warp == 1) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                   : "memory");
+  }
 }
 
 // ---- cluster kernel: the 8 CTAs of a cluster share the raw ciphertexts ----
@@ -1177,37 +1400,6 @@ struct ClusterParams {
   CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 2 clients)
   TcLimb limb[GPIR_MAX_LIMBS];
 };
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// Address of the same shared-memory offset in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t map_peer(uint32_t local_saddr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_saddr), "r"(rank));
-  return r;
-}
-// Arrive on barrier `bar` (same offset) in every CTA of `mask` once the
-// MMAs issued so far have completed.
-__device__ __forceinline__ void mma_commit_cluster(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
 
 template <bool PROF>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_cluster_kernel(const __grid_constant__ ClusterParams p) {
@@ -1873,7 +2065,7 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
 
 // Fused-kernel tile variants: digit-ring size (against the 129 MB L2) and L2
 // eviction hints; the autotuner picks one per shape.
-enum TcKernelKind : uint32_t { kKindFused = 0, kKindTwoPass = 1, kKindCluster = 2 };
+enum TcKernelKind : uint32_t { kKindFused = 0, kKindTwoPass = 1, kKindCluster = 2, kKindPair = 3 };
 struct FusedVariant {
   uint32_t kind;           // TcKernelKind
   uint32_t ring_mb;
@@ -1889,34 +2081,73 @@ constexpr FusedVariant kFusedVariants[] = {
     {kKindFused, 48, kHintRing, 16},    // 4
     {kKindFused, 40, kHintRing, 16},    // 5
     {kKindCluster, 0, 0, 0},            // 6: 8-CTA clusters sharing raw boxes over DSMEM
+    {kKindPair, 48, 0, 16},             // 7: SM pairs (cta_group::2) sharing each database tile
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
 std::mutex g_fused_attr_mu;
 bool g_fused_attr_done[64];
+int g_pair_clusters[64];   // resident CTA pairs of the pair kernel per device (0: not queried yet, -1: none)
+
+cudaLaunchConfig_t pair_config(unsigned grid, cudaStream_t stream, cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(FUSED_THREADS);
+  cfg.dynamicSmemBytes = PAIR_SMEM;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
 
 // One RowSel problem through the fused persistent kernel (ingest warps and
 // GEMM warps in one launch; digit tiles only pass through an L2-sized ring).
+// pair: the SM-pair form (cta_group::2); GPIR_ENOTSUP when the batch has an
+// odd number of 32-row m-blocks or no CTA pair can be resident.
 int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                    uint32_t hints, uint32_t lookahead_mb, cudaStream_t stream) {
+                    uint32_t hints, uint32_t lookahead_mb, bool pair, cudaStream_t stream) {
   if (!db->db_digits) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e);
   if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  const TcShape sh = tc_shape(db, batch);
+  if (pair && (sh.mblk & 1u)) return GPIR_ENOTSUP;
   {
     std::lock_guard<std::mutex> lk(g_fused_attr_mu);
     if (!g_fused_attr_done[dev]) {
-      e = cudaFuncSetAttribute(tc_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+      e = cudaFuncSetAttribute(tc_fused_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)FUSED_SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM);
+        e = cudaFuncSetAttribute(tc_fused_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FUSED_SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fused_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PAIR_SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_fused_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PAIR_SMEM);
       if (e != cudaSuccess) return set_cuda_error(e);
+      cudaLaunchAttribute attr[1];
+      const cudaLaunchConfig_t cfg = pair_config((unsigned)(sm_count() / 2 * 2), nullptr, attr);
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, tc_fused_kernel<false, true>, &cfg);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+      g_pair_clusters[dev] = n > 0 ? n : -1;
       g_fused_attr_done[dev] = true;
     }
   }
+  if (pair && g_pair_clusters[dev] < 0) return GPIR_ENOTSUP;
   const gpir_params &prm = db->params;
   const uint32_t L = prm.num_limbs, N = prm.n;
-  const TcShape sh = tc_shape(db, batch);
   FusedParams fp;
   memset(&fp, 0, sizeof(fp));
   fp.L = L;
@@ -1931,7 +2162,7 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.n_entries = (uint64_t)fp.gpl * L * sh.mblk;
   fp.spg = N < 8 ? N : 8u;                      // N is a power of two >= 4
   fp.upe = (uint64_t)fp.spg * sh.nblk;          // units per entry: valid slots x n-blocks
-  fp.n_units = fp.n_entries * fp.upe;
+  fp.n_units = (pair ? fp.n_entries / 2 : fp.n_entries) * fp.upe;   // pair: a unit covers two entries
   fp.n_tasks = fp.n_entries * sh.kch;
   const size_t entry_bytes = (size_t)8 * sh.kch * A_TILE_BYTES;
   uint64_t R = ring_target / entry_bytes;
@@ -1966,12 +2197,25 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.lookahead = lookahead_mb == 0 ? 0u : (uint32_t)std::max<uint64_t>(2, ((uint64_t)lookahead_mb << 20) / entry_bytes);
   fp.err = device_error_word();
   for (uint32_t l = 0; l < L; ++l) fp.limb[l] = make_limb(prm.primes[l]);
+  if (pair) {
+    // every CTA pair stays resident (persistent kernel): at most the pairs that fit at once
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = pair_config((unsigned)(2 * g_pair_clusters[dev]), stream, attr);
+    const int tr = trace_begin("tc_pair", stream);
+    e = fp.prof ? cudaLaunchKernelEx(&cfg, tc_fused_kernel<true, true>, fp)
+                : cudaLaunchKernelEx(&cfg, tc_fused_kernel<false, true>, fp);
+    trace_end(tr, stream);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (fp.prof) trace_counters(fp.prof, kNumFusedCounters, stream);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+  }
   const int grid = sm_count();
   const int tr = trace_begin("tc_fused", stream);
   if (fp.prof)
-    tc_fused_kernel<true><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+    tc_fused_kernel<true, false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
   else
-    tc_fused_kernel<false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
+    tc_fused_kernel<false, false><<<grid, FUSED_THREADS, FUSED_SMEM, stream>>>(fp);
   trace_end(tr, stream);
   if (fp.prof) trace_counters(fp.prof, kNumFusedCounters, stream);
   e = cudaGetLastError();
@@ -2095,7 +2339,7 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
   if (v.kind == kKindCluster) {
     const int rc = tc_launch_cluster(db, batch, ct, out, stream);
     if (rc != GPIR_ENOTSUP) return rc;
-    return tc_launch_fused(db, batch, ct, out, (size_t)48 << 20, 0, 16, stream);   // N < 8 or no cluster fits
+    return tc_launch_fused(db, batch, ct, out, (size_t)48 << 20, 0, 16, false, stream);   // N < 8 or no cluster fits
   }
   if (v.kind == kKindTwoPass) {
     gpir_job_t job;
@@ -2106,7 +2350,13 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
   }
-  return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, stream);
+  if (v.kind == kKindPair) {
+    const int rc = tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, true, stream);
+    if (rc != GPIR_ENOTSUP) return rc;
+    // an odd number of m-blocks (or no pair fits): the single-CTA form
+    return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, false, stream);
+  }
+  return tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, false, stream);
 }
 
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs) {

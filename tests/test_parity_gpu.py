@@ -142,8 +142,9 @@ def test_one_hot_returns_row(g, path):
             assert np.array_equal(got[c, :, r], db[i])
 
 
-def _sampled_full_size(g, name, path, n_slots=6):
-    """Full-size workload generated on the device; oracle on sampled slots."""
+def _sampled_full_size(g, name, path, n_slots=6, variant=None):
+    """Full-size workload generated on the device; oracle on sampled slots
+    (`variant`: a tile variant to force, else the library's choice)."""
     import torch
     from tests.gpu_util import to_host
     _skip_unbuilt(g, path)
@@ -159,6 +160,8 @@ def _sampled_full_size(g, name, path, n_slots=6):
     del db_d
     out = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
     try:
+        if variant is not None:
+            g.gpir_set_variant(h, B, path, variant)
         g.gpir_rowsel_batch(h, B, ct_d, out, path)
         torch.cuda.synchronize()
         g.gpir_sync(None, 60000)
