@@ -71,11 +71,14 @@ def test_rowsel_vs_oracle(g, shape, path):
     _check_full(g, B, D0, D1, L, N, primes, seed, PATHS[path])
 
 
+@pytest.mark.parametrize("B", [6, 17])
 @pytest.mark.parametrize("path", PATH_LIST)
-def test_every_variant(g, path):
+def test_every_variant(g, path, B):
+    """Every compiled tile variant of every path; B = 17 gives the tensor-core
+    kernels two 32-row m-blocks (the SM-pair variant runs as pairs)."""
     p = PATHS[path]
     nv = g.gpir_num_variants(p)
-    _check_full(g, 6, 70, 40, 2, 64, synth.PRIMES_28, 77, p, variants=list(range(nv)))
+    _check_full(g, B, 70, 40, 2, 64, synth.PRIMES_28, 77 + B, p, variants=list(range(nv)))
 
 
 @pytest.mark.parametrize("path", PATH_LIST)
