@@ -660,10 +660,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(const __grid_c
 //   - the even CTA's producer claims units and hands each to the odd CTA's
 //     producer through a 4-slot mailbox (remote store + release arrive);
 //   - the odd CTA's warp 1 relays "my operands of stage st have landed" to the
-//     even CTA's pfull[st];
+//     even CTA's pfull[st] (a relaxed remote arrive: it carries no data of the
+//     relaying thread, and a cluster-scope release would wait for the SM's
+//     outstanding ring stores);
 //   - MMA commits arrive on empty[st] and acc_full[b] in both CTAs
 //     (multicast), and the odd CTA's epilogue warps also arrive on the even
-//     CTA's acc_empty[b] (count 16 there);
+//     CTA's acc_empty[b] (count 16 there; relaxed too, after their
+//     tensor-memory loads have completed);
 //   - each CTA's epilogue, store warp and ring accounting work on its own
 //     entry 2 E2 + rank, exactly as in the single-CTA form.
 // Both CTAs walk the same unit sequence, so their stage and accumulator
