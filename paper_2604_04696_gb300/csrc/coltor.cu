@@ -37,8 +37,9 @@
 // digit's first round need no barrier between them: 98.8 KB (limb kernel) or
 // 82.3 KB (split kernel) at N = 4096, two CTAs per SM, so that their phases
 // (transform-bound, load-bound) overlap. The multiply-accumulate keeps 64-bit
-// sums in registers: each of the at most 2 ell terms is below 4q * q < 2^58,
-// so the sum stays below 2^61 and one Barrett reduction per output finishes it.
+// sums in registers: each of the at most 2 ell <= 6 terms is below
+// 14q * q < 2^60 (the forward transform's lazy range times a key residue), so
+// the sum stays below 2^63 and one Barrett reduction per output finishes it.
 
 #include <cuda.h>
 #include <cuda_runtime.h>

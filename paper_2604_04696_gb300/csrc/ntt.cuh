@@ -93,12 +93,23 @@ __device__ __forceinline__ uint32_t shoup(uint32_t a, uint32_t w, uint32_t ws, u
 __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t q) { return csub(a + b, q); }
 __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t q) { return csub(a - b + q, q); }
 
-// Cooley-Tukey butterfly, inputs and outputs in [0, 4q).
+// Cooley-Tukey butterfly with no reduction of its own: t = w y mod q lies in
+// [0, 2q) for any 32-bit y (Shoup), so x < B gives outputs below B + 2q. Each
+// forward round first brings its values below 8q (fwd_entry), so after its at
+// most three levels they stay below 14q < 2^32 (q < 2^28): one conditional
+// subtraction per value and round instead of one per butterfly.
 __device__ __forceinline__ void ct(uint32_t &x, uint32_t &y, uint32_t w, uint32_t ws, uint32_t q) {
-  const uint32_t u = csub(x, 2 * q);
   const uint32_t t = shoup_lazy(y, w, ws, q);
+  const uint32_t u = x;
   x = u + t;
   y = u - t + 2 * q;
+}
+// Start of a forward round: values below 16q (14q from the previous round,
+// q for the input coefficients) are brought below 8q.
+template <int K>
+__device__ __forceinline__ void fwd_entry(uint32_t (&v)[8], uint32_t q) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = csub(v[k], 8 * q);
 }
 // Gentleman-Sande butterfly, inputs and outputs in [0, 2q).
 __device__ __forceinline__ void gs(uint32_t &x, uint32_t &y, uint32_t w, uint32_t ws, uint32_t q) {
@@ -116,6 +127,7 @@ __device__ __forceinline__ uint2 ld2(const uint2 *p) { return __ldg(p); }
 // Level r pairs k with k + 2^(R-1-r) and uses twiddle 2^r M0 + 2^r i + (k >> (R-r)).
 template <int R, uint32_t M0>
 __device__ __forceinline__ void fwd_round(uint32_t (&v)[8], const uint2 *fw, uint32_t i, uint32_t q) {
+  fwd_entry<(1 << R)>(v, q);
   if constexpr (R == 3) {
     const uint2 a = ld2(fw + i + M0);
     ct(v[0], v[4], a.x, a.y, q); ct(v[1], v[5], a.x, a.y, q); ct(v[2], v[6], a.x, a.y, q); ct(v[3], v[7], a.x, a.y, q);
@@ -164,6 +176,7 @@ __device__ __forceinline__ void inv_round(uint32_t (&v)[8], const uint2 *iv, uin
 //   fw_last[b]  = W[N/8 + i], W[N/4 + 2i], W[N/4 + 2i + 1], -, W[N/2 + 4i + 0..3]
 //   iv_first[b] = V[N/2 + 4i + 0..3], V[N/4 + 2i], V[N/4 + 2i + 1], V[N/8 + i], -
 __device__ __forceinline__ void fwd_round_last(uint32_t (&v)[8], const uint2 *t, uint32_t q) {
+  fwd_entry<8>(v, q);
   const uint4 a = ld4(t), b = ld4(t + 2);
   ct(v[0], v[4], a.x, a.y, q); ct(v[1], v[5], a.x, a.y, q); ct(v[2], v[6], a.x, a.y, q); ct(v[3], v[7], a.x, a.y, q);
   ct(v[0], v[2], a.z, a.w, q); ct(v[1], v[3], a.z, a.w, q); ct(v[4], v[6], b.x, b.y, q); ct(v[5], v[7], b.x, b.y, q);
@@ -263,8 +276,8 @@ __device__ __forceinline__ void inv_middles(uint32_t *const (&buf)[P], const Lim
 }
 
 // Forward NTT of P polynomials of one limb (one padded buffer of padn(N) words
-// each). In: v[p][k] = coefficient b + (N/8) k, values < 4q. Out: v[p][e] =
-// slot b + (N/8) e, values in [0, 4q). Every thread of the CTA must call it
+// each). In: v[p][k] = coefficient b + (N/8) k, values < 16q. Out: v[p][e] =
+// slot b + (N/8) e, values in [0, 14q) (lazy: congruent mod q, not reduced). Every thread of the CTA must call it
 // (it holds __syncthreads); act = b < N/8. The buffers are free again once
 // the next barrier of the CTA has passed.
 template <int LOGN, int P>
