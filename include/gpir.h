@@ -160,6 +160,16 @@ int gpir_graph_destroy(gpir_graph_t *graph);
  * the stream reported an error. */
 int gpir_sync(void *stream, uint32_t timeout_ms);
 
+/* Self-test of the device-side failure path. Enqueues on `stream` one kernel
+ * whose single thread waits, through the same bounded mbarrier wait the RowSel
+ * kernels use, on a barrier that nothing ever arrives on. The wait gives up
+ * after its limit (2 s), records the expiry in the device error word and the
+ * kernel returns normally: no trap, no hang, the context stays usable. A
+ * following gpir_sync(stream, t) with t > 2000 then returns GPIR_ETIMEOUT and
+ * clears the word, so the sync after it returns GPIR_OK. Asynchronous;
+ * GPIR_ECUDA if the launch fails. */
+int gpir_selftest_bounded_wait(void *stream);
+
 /* Autotuner: time every compiled tile variant of `path` (three runs each,
  * after a warm-up) for `batch` clients against this database, using the
  * caller's device buffers ct_dev / out_dev (layouts as in gpir_rowsel_batch;

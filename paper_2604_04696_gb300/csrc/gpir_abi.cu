@@ -192,6 +192,17 @@ static int num_variants(int path) {
 
 using namespace gpir;
 
+// One thread waits on an mbarrier that nothing arrives on (phase 0 never
+// completes), through the bounded wait of the RowSel kernels.
+static __global__ void selftest_wait_kernel(unsigned int *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    gpir::mbar_init(&bar, 1);
+    gpir::fence_mbar_init();
+    gpir::mbar_wait_bounded(&bar, 0, err, gpir::kErrQueueWait);
+  }
+}
+
 extern "C" {
 
 int gpir_version(void) { return 100; }
@@ -507,6 +518,14 @@ int gpir_sync(void *stream, uint32_t timeout_ms) {
     return GPIR_ETIMEOUT;
   }
   return GPIR_OK;
+}
+
+int gpir_selftest_bounded_wait(void *stream) {
+  unsigned int *w = device_error_word();
+  if (!w) return GPIR_ECUDA;
+  selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(w);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
 
 int gpir_num_variants(int path) { return num_variants(path); }

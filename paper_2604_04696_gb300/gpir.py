@@ -73,6 +73,7 @@ def _load():
         "gpir_graph_launch": (I, [P, P]),
         "gpir_graph_destroy": (I, [P]),
         "gpir_sync": (I, [P, U32]),
+        "gpir_selftest_bounded_wait": (I, [P]),
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
         "gpir_selected_variant": (I, [P, U32, I]),
@@ -205,6 +206,10 @@ def gpir_graph_destroy(graph):
 
 def gpir_sync(stream=None, timeout_ms=0):
     return _check(lib.gpir_sync(_stream(stream), int(timeout_ms)), "gpir_sync")
+
+
+def gpir_selftest_bounded_wait(stream=None):
+    return _check(lib.gpir_selftest_bounded_wait(_stream(stream)), "gpir_selftest_bounded_wait")
 
 
 def gpir_sync_rc(stream=None, timeout_ms=0):
