@@ -16,7 +16,9 @@
 // and  x*y = sum_{u,v} a_u b_v 2^(8(u+v)), so
 //     out = sum_groups sum_{u,v} D_uv * (2^(8(u+v)) mod q)   (mod q),
 // computed in 64-bit integers in the epilogue. The K dimension is processed in
-// groups of 256 rows, each group accumulating in its own tensor-memory buffer.
+// groups of 256 rows (two-pass kernel) or 512 rows (fused, pair and cluster
+// kernels, |D| <= 2^23, still exact), each group accumulating in its own
+// tensor-memory buffer.
 //
 // GEMM shape. One MMA instruction computes all 16 digit pairs at once: the A
 // operand stacks the 4 digits of 32 ciphertext rows (M' = 128 rows, ordered
@@ -28,14 +30,20 @@
 //
 // Data movement. The DB is stored once, at upload, as per-slot digit tiles
 // already in the shared-memory image the MMA reads (K-major, 128-byte
-// swizzle): [slot][n-block][k-chunk] x (256 rows x 64 k) fp16. Per batch, an
-// ingest kernel turns the p-major ciphertexts into the same image for the A
-// operand ([slot][m-block][k-chunk] x (128 rows x 64 k)), reading 8 slots
-// (one 32-byte sector) per row. The persistent GEMM kernel streams both with
-// 1-D bulk copies into a 4-stage mbarrier ring (one producer warp), one thread
-// issues the MMAs, sixteen epilogue warps drain tensor memory (double-buffered
-// accumulators, so draining overlaps the next group's MMAs) and write the
-// canonical residues in the p-major output layout.
+// swizzle): [slot][n-block][k-chunk] x (256 rows x 64 k) fp16. Per batch the
+// p-major ciphertexts are split into the same image for the A operand,
+// reading 8 slots (one 32-byte sector) per row, in one of four forms:
+//   - fused (default): persistent CTAs whose ingest warps write the A tiles
+//     into an L2-sized ring in global memory while their GEMM warps stream A
+//     and B tiles with bulk copies into shared-memory stages, one thread issues
+//     the MMAs, epilogue warps drain tensor memory (double-buffered) and a
+//     store warp writes the p-major output;
+//   - SM pair: the fused kernel on 2-CTA clusters with cta_group::2 MMAs
+//     (M = 256) that share one database tile between the two SMs;
+//   - two-pass: an ingest kernel writes every A tile to HBM, then a persistent
+//     GEMM kernel reads them (also the multi-job form);
+//   - cluster: 8-CTA clusters, one CTA per slot of a group, exchange the digit
+//     rows through distributed shared memory, so no A tile leaves the cluster.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
