@@ -105,8 +105,9 @@ size_t gpir_db_device_bytes(const gpir_db_t *db);
  * for every client c < batch, output ct j < D1, polynomial r < 2, limb l and
  * slot t. `ct_dev` and `out_dev` are device buffers in the layouts above and
  * must not overlap. Inputs must be canonical residues (< q_l): this is a
- * precondition, not checked, because a check would add a pass over the
- * ciphertext stream. Results are canonical and identical for every path.
+ * precondition, checked only with the debug checks on (gpir_set_debug),
+ * because a check adds a pass over the ciphertext stream. Results are
+ * canonical and identical for every path.
  * GPIR_ENOTSUP if `path` was not prepared at upload. The tensor-core path
  * keeps its per-batch digit tiles (2x the ciphertext bytes) in a workspace
  * owned by the library per (device, stream), grown on demand; calls on
@@ -159,6 +160,17 @@ int gpir_graph_destroy(gpir_graph_t *graph);
  * reported that one of its bounded device-side waits expired; GPIR_ECUDA if
  * the stream reported an error. */
 int gpir_sync(void *stream, uint32_t timeout_ms);
+
+/* Debug checks (off by default; on when the environment variable GPIR_DEBUG
+ * is a nonzero number when the library first needs the setting, or after
+ * gpir_set_debug(1)). While on, gpir_rowsel_batch, gpir_rowsel_batch_noalloc,
+ * gpir_rowsel_multi and gpir_rowsel_batch_host first check that every
+ * ciphertext residue is below its limb's prime and return GPIR_ERANGE,
+ * computing nothing, if one is not. The device-side check synchronizes
+ * `stream` (so these calls are not asynchronous and cannot be captured into a
+ * CUDA graph while it is on); the host entry checks its host buffer on the
+ * CPU. Returns the previous setting (0 or 1). */
+int gpir_set_debug(int on);
 
 /* Self-test of the device-side failure path. Enqueues on `stream` one kernel
  * whose single thread waits, through the same bounded mbarrier wait the RowSel

@@ -13,12 +13,16 @@
 #include <new>
 #include <thread>
 
+#include <atomic>
+#include <cstdlib>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace gpir {
 
 static __device__ unsigned int g_device_error = 0;
+static __device__ unsigned int g_range_flag = 0;   // debug checks: a residue >= q was seen
 
 static thread_local cudaError_t t_last_cuda_error = cudaSuccess;
 
@@ -40,6 +44,21 @@ unsigned int *device_error_word() {
   if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
   cache[dev] = (unsigned int *)p;
   return (unsigned int *)p;
+}
+
+// Debug checks: -1 = not read yet, else 0 / 1.
+static std::atomic<int> g_debug{-1};
+
+bool debug_checks() {
+  int d = g_debug.load(std::memory_order_relaxed);
+  if (d < 0) {
+    const char *v = std::getenv("GPIR_DEBUG");
+    d = (v && std::strtol(v, nullptr, 10) != 0) ? 1 : 0;
+    int expect = -1;
+    g_debug.compare_exchange_strong(expect, d);
+    d = g_debug.load(std::memory_order_relaxed);
+  }
+  return d == 1;
 }
 
 int sm_count() {
@@ -101,6 +120,32 @@ __global__ void range_check_kernel(const uint32_t *__restrict__ v, uint64_t coun
     local |= (v[i] >= limbs.m[l].q) ? 1u : 0u;
   }
   if (local) atomicOr(bad, 1u);
+}
+
+int check_residues_dev(const gpir_params &prm, const uint32_t *v, uint64_t count, cudaStream_t s) {
+  static std::mutex mu;                       // one check at a time: they share the device flag
+  static std::map<int, unsigned int *> flags;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = flags.find(dev);
+  if (it == flags.end()) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_range_flag);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    it = flags.emplace(dev, static_cast<unsigned int *>(p)).first;
+  }
+  if (count == 0) return GPIR_OK;
+  unsigned int *flag = it->second;
+  e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  range_check_kernel<<<sm_count() * 4, 256, 0, s>>>(v, count, prm.n, prm.num_limbs, prm.limbs, flag);
+  unsigned int h = 0;
+  e = cudaMemcpyAsync(&h, flag, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  return h ? GPIR_ERANGE : GPIR_OK;
 }
 
 __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
@@ -339,6 +384,7 @@ size_t gpir_db_device_bytes(const gpir_db_t *db) {
 
 int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
                       void *stream) {
+  NvtxRange nvtx("gpir_rowsel_batch");
   if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
   int p = resolve_path(db, path, batch);
   if (p == -1) return GPIR_EINVAL;
@@ -348,12 +394,17 @@ int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_de
   const uintptr_t a0 = (uintptr_t)ct_dev, a1 = a0 + ct_bytes, b0 = (uintptr_t)out_dev, b1 = b0 + out_bytes;
   if (a0 < b1 && b0 < a1) return GPIR_EINVAL;  // overlapping input / output
   if ((a0 & 15u) || (b0 & 15u)) return GPIR_EINVAL;
+  if (debug_checks()) {
+    const int rc = check_residues_dev(db->params, ct_dev, ct_bytes / 4, (cudaStream_t)stream);
+    if (rc != GPIR_OK) return rc;
+  }
   return dispatch(db, batch, ct_dev, out_dev, p, pick_variant(db, batch, p), (cudaStream_t)stream);
 }
 
 int gpir_pir_batch(const gpir_db_t *db, uint32_t batch, uint32_t stages, const uint32_t *query_dev,
                    const uint32_t *evk_dev, const uint32_t *rgsw_dev, uint32_t *sel_dev, uint32_t *rows_dev,
                    uint32_t *out_dev, int path, void *stream) {
+  NvtxRange nvtx("gpir_pir_batch");
   if (!db || batch == 0 || !query_dev || !rgsw_dev || !sel_dev || !rows_dev || !out_dev) return GPIR_EINVAL;
   if (db->d1 < 2 || (db->d1 & (db->d1 - 1)) != 0) return GPIR_EINVAL;
   if (stages >= 32 || db->d0 > (1u << stages)) return GPIR_EINVAL;
@@ -404,8 +455,16 @@ int host_pipe(int dev, HostPipe **out) {
 
 int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t *ct_host, uint32_t *out_host,
                            int path, void *stream) {
+  NvtxRange nvtx("gpir_rowsel_batch_host");
   if (!db_c || !ct_host || !out_host || batch == 0) return GPIR_EINVAL;
   gpir_db *db = const_cast<gpir_db *>(db_c);
+  if (debug_checks()) {
+    // the host buffer, on the CPU: residue i belongs to limb (i / N) % L
+    const uint32_t L = db->params.num_limbs, N = db->params.n;
+    const uint64_t count = (uint64_t)batch * db->d0 * 2 * L * N;
+    for (uint64_t i = 0; i < count; ++i)
+      if (ct_host[i] >= db->params.limbs.m[(i / N) % L].q) return GPIR_ERANGE;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t ct_client = (size_t)db->d0 * 2 * db->params.num_limbs * db->params.n * 4;
   const size_t out_client = (size_t)db->d1 * 2 * db->params.num_limbs * db->params.n * 4;
@@ -486,6 +545,7 @@ int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t
 }
 
 int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream) {
+  NvtxRange nvtx("gpir_rowsel_multi");
   if (!jobs || njobs == 0) return GPIR_EINVAL;
   for (uint32_t k = 0; k < njobs; ++k) {
     if (!jobs[k].db || !jobs[k].ct || !jobs[k].out || jobs[k].batch == 0) return GPIR_EINVAL;
@@ -493,6 +553,13 @@ int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *st
     if (a.n != b.n || a.num_limbs != b.num_limbs || memcmp(a.primes, b.primes, sizeof(a.primes)) != 0)
       return GPIR_EINVAL;
   }
+  if (debug_checks())
+    for (uint32_t k = 0; k < njobs; ++k) {
+      const gpir_params &prm = jobs[k].db->params;
+      const uint64_t count = (uint64_t)jobs[k].batch * jobs[k].db->d0 * 2 * prm.num_limbs * prm.n;
+      const int rc = check_residues_dev(prm, jobs[k].ct, count, (cudaStream_t)stream);
+      if (rc != GPIR_OK) return rc;
+    }
   return rowsel_multi_launch(jobs, njobs, path, (cudaStream_t)stream);
 }
 
@@ -526,6 +593,12 @@ int gpir_selftest_bounded_wait(void *stream) {
   selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(w);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+int gpir_set_debug(int on) {
+  const int prev = debug_checks() ? 1 : 0;
+  g_debug.store(on ? 1 : 0);
+  return prev;
 }
 
 int gpir_num_variants(int path) { return num_variants(path); }

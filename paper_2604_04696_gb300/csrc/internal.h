@@ -11,6 +11,8 @@
 
 #include "../../include/gpir.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace gpir {
 
 // Per-limb modulus data passed by value to kernels.
@@ -72,6 +74,20 @@ int encode_tiled(CUtensorMap *map, CUtensorMapDataType dt, const void *base, int
 // Device error word written by bounded waits in kernels (0 = ok).
 unsigned int *device_error_word();
 int sm_count();
+
+// Debug checks (gpir_set_debug / GPIR_DEBUG): on or off.
+bool debug_checks();
+// Debug check of a device tensor whose two innermost dimensions are [L][N]:
+// GPIR_ERANGE if a residue is not below its limb's prime. Synchronizes s;
+// allocates nothing.
+int check_residues_dev(const gpir_params &prm, const uint32_t *v, uint64_t count, cudaStream_t s);
+
+// Scoped NVTX range around an ABI call (a no-op unless a profiler injects
+// itself).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Path entry points (one per translation unit).
 int rowsel_cc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out,

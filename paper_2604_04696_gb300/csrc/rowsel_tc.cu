@@ -2446,6 +2446,7 @@ int noalloc_setup(int dev, void **tiles) {
 extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                                          uint32_t *out_dev, void *stream) {
   using namespace gpir;
+  NvtxRange nvtx("gpir_rowsel_batch_noalloc");
   if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
   if (!(db->path_mask & GPIR_PATH_TC) || !db->db_digits) return GPIR_ENOTSUP;
   const uint32_t L = db->params.num_limbs, N = db->params.n, M = 2 * batch;
@@ -2471,6 +2472,10 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
   job.reserved = 0;
   job.ct = ct_dev;
   job.out = out_dev;
+  if (debug_checks()) {
+    rc = check_residues_dev(db->params, ct_dev, ct_bytes / 4, (cudaStream_t)stream);
+    if (rc != GPIR_OK) return rc;
+  }
   const size_t off = 0;
   return tc_launch_jobs(&job, 1, reinterpret_cast<uint8_t *>(tiles), &off, (cudaStream_t)stream);
 }

@@ -74,6 +74,7 @@ def _load():
         "gpir_graph_destroy": (I, [P]),
         "gpir_sync": (I, [P, U32]),
         "gpir_selftest_bounded_wait": (I, [P]),
+        "gpir_set_debug": (I, [I]),
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
         "gpir_selected_variant": (I, [P, U32, I]),
@@ -206,6 +207,11 @@ def gpir_graph_destroy(graph):
 
 def gpir_sync(stream=None, timeout_ms=0):
     return _check(lib.gpir_sync(_stream(stream), int(timeout_ms)), "gpir_sync")
+
+
+def gpir_set_debug(on=True):
+    """Debug checks of the ciphertext residues on or off; returns the previous setting."""
+    return lib.gpir_set_debug(1 if on else 0)
 
 
 def gpir_selftest_bounded_wait(stream=None):

@@ -180,3 +180,19 @@ def test_tree_and_pipeline_argument_errors_on_the_host(g):
             assert g.lib.gpir_expand_query(p3, 1, 1, 2, 1 << 40, 2 << 40, 3 << 40, None) == g.GPIR_ENOTSUP
         finally:
             g.gpir_params_destroy(p3)
+
+
+def test_debug_switch_and_environment():
+    """gpir_set_debug returns the previous setting; GPIR_DEBUG=1 in the
+    environment turns the checks on when the library first reads it."""
+    import subprocess
+    import sys
+    code = ("from paper_2604_04696_gb300 import gpir as g; "
+            "a = g.gpir_set_debug(True); b = g.gpir_set_debug(False); c = g.gpir_set_debug(False); print(a, b, c)")
+    env = dict(os.environ)
+    env.pop("GPIR_DEBUG", None)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    assert r.stdout.split() == ["0", "1", "0"]
+    env["GPIR_DEBUG"] = "1"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    assert r.stdout.split() == ["1", "1", "0"]

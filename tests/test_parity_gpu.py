@@ -319,3 +319,42 @@ def test_auto_path_after_autotune(g, B):
         assert np.array_equal(got, want)
     finally:
         h.close()
+
+
+def test_debug_checks_reject_non_canonical_ciphertexts(g):
+    """With the debug checks on, every RowSel entry point refuses a ciphertext
+    residue that is not below its limb's prime (GPIR_ERANGE, nothing computed)
+    and still computes canonical inputs bit-exactly; with them off the
+    precondition is not checked."""
+    import torch
+    from tests.gpu_util import DbHandle, to_dev, to_host, make_problem
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 3, 40, 24, 2, 64
+    ct, db = make_problem(91, B, D0, D1, L, N, primes)
+    want = oracle.rowsel(ct, db, list(primes))
+    bad = ct.copy()
+    bad[1, 7, 1, 1, 5] = primes[1]          # equal to q1, in limb 1
+    h = DbHandle(g, db, N, primes, path_mask=0)
+    prev = g.gpir_set_debug(True)
+    try:
+        for path in [p for p in (1, 2, 4) if g.gpir_num_variants(p) > 0]:
+            assert np.array_equal(to_host(h.rowsel(to_dev(ct), B, path)), want), path
+            with pytest.raises(g.GpirError) as ei:
+                h.rowsel(to_dev(bad), B, path)
+            assert ei.value.code == g.GPIR_ERANGE, path
+        out = torch.empty((B, D1, 2, L, N), dtype=torch.int32, device="cuda")
+        with pytest.raises(g.GpirError) as ei:
+            g.gpir_rowsel_multi([(h.h, B, to_dev(bad), out)], 0)
+        assert ei.value.code == g.GPIR_ERANGE
+        if g.gpir_num_variants(4) > 0:
+            with pytest.raises(g.GpirError) as ei:
+                g.gpir_rowsel_batch_noalloc(h.h, B, to_dev(bad), out)
+            assert ei.value.code == g.GPIR_ERANGE
+        out_h = np.zeros((B, D1, 2, L, N), dtype=np.uint32)
+        with pytest.raises(g.GpirError) as ei:
+            g.gpir_rowsel_batch_host(h.h, B, np.ascontiguousarray(bad), out_h, 1)
+        assert ei.value.code == g.GPIR_ERANGE
+    finally:
+        g.gpir_set_debug(prev)
+    h.rowsel(to_dev(bad), B, 1)              # off: accepted (the result is unspecified)
+    h.close()
