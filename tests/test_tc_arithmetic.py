@@ -121,3 +121,77 @@ def test_model_equals_oracle(shape):
     ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
     db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
     assert np.array_equal(tc_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
+
+
+MAGIC = 0x4B400000          # bit pattern of 1.5 * 2^23 in fp32
+GROUP2 = 256                # rows per exact group in the two-pass kernel
+
+
+def magic_bits(D):
+    """Bit pattern of fp32(D) + 1.5 * 2^23, as the two-pass epilogue forms it."""
+    return (np.asarray(D, dtype=np.float32) + np.float32(12582912.0)).view(np.int32).astype(np.int64)
+
+
+def test_magic_conversion_exact_within_2_22():
+    """fp32 D + 1.5 * 2^23 has bit pattern MAGIC + D exactly for |D| <= 2^22,
+    the bound of a 256-row group of digit products (256 * 2^14)."""
+    rng = np.random.default_rng(3)
+    D = np.concatenate([rng.integers(-(1 << 22), (1 << 22) + 1, 100000), [0, 1, -1, 1 << 22, -(1 << 22)]])
+    assert np.array_equal(magic_bits(D) - MAGIC, D)
+    # negative control: one past the bound the spacing is 2 (above) or the scale changes (below)
+    assert magic_bits((1 << 22) + 1) - MAGIC != (1 << 22) + 1
+    assert magic_bits(-(1 << 22) - 1) - MAGIC != -(1 << 22) - 1
+
+
+def test_two_pass_sum_bound():
+    """sum over the 16 digit pairs of bits * c stays below 2^63 for the real
+    primes: bits <= MAGIC + 2^22 and c < q."""
+    for q in PRIMES:
+        assert 16 * (MAGIC + (1 << 22)) * (int(q) - 1) < 1 << 63
+
+
+def tc_model_rowsel_two_pass(ct, db, primes):
+    """The two-pass epilogue: 256-row groups, magic conversion, kfix removed,
+    one Barrett reduction (offset by a multiple of q >= 2^55) per group."""
+    ct = np.asarray(ct)
+    db = np.asarray(db)
+    B, D0, _, L, T = ct.shape
+    D1 = db.shape[1]
+    out = np.zeros((B, D1, 2, L, T), dtype=np.uint64)
+    for l, q in enumerate(primes):
+        q = int(q)
+        c = [pow(2, 8 * s, q) for s in range(7)]
+        kfix = MAGIC * sum(c[u + v] for u in range(4) for v in range(4))
+        off = -(-(1 << 55) // q) * q
+        for t in range(T):
+            a = digits(ct[:, :, :, l, t].transpose(0, 2, 1).reshape(2 * B, D0))
+            bd = digits(db[:, :, l, t])
+            res = np.zeros((2 * B, D1), dtype=object)
+            for g0 in range(0, D0, GROUP2):
+                g1 = min(D0, g0 + GROUP2)
+                keep = np.zeros((2 * B, D1), dtype=object)
+                for u in range(4):
+                    for v in range(4):
+                        Dm = a[:, g0:g1, u].astype(np.float32) @ bd[g0:g1, :, v].astype(np.float32)
+                        assert np.all(np.abs(Dm) <= 1 << 22)
+                        keep = keep + magic_bits(Dm).astype(object) * c[u + v]
+                x = keep - kfix + off
+                assert all(0 <= int(v) < 1 << 64 for v in np.ravel(x))
+                res = (res + x % q) % q
+            out[:, :, :, l, t] = res.astype(np.uint64).reshape(B, 2, D1).transpose(0, 2, 1)
+    return out.astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", [(2, 600, 5, 2, 2), (1, 256, 3, 1, 2)])
+def test_two_pass_model_equals_oracle(shape):
+    """Random residues and the all-(q-1) worst case; D0 = 600 spans three groups
+    (the last one ragged)."""
+    B, D0, D1, L, T = shape
+    primes = PRIMES[:L]
+    ct = synth.uniform_residues(71 + D0, synth.TAG_CT, (B, D0, 2, L, T), primes, limb_axis=3)
+    db = synth.uniform_residues(72 + D0, synth.TAG_DB, (D0, D1, L, T), primes, limb_axis=2)
+    assert np.array_equal(tc_model_rowsel_two_pass(ct, db, primes), oracle.rowsel(ct, db, primes))
+    qm = np.array(primes, dtype=np.uint32)
+    ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
+    db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
+    assert np.array_equal(tc_model_rowsel_two_pass(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
