@@ -8,9 +8,9 @@
 // C_s = sum_{u+v=s} x_u y_v (s = 0..6). The tensor core forms, exactly in
 // int32, A_s = sum_k sum_{u+v=s} a_u[m][k] b_v[k][n] with one
 // mma.sync.m16n8k32.u8.u8.s32 per digit pair (u, v) into accumulator set s.
-// Bound: C_3 has the most pairs, sum <= 2*255*15 + 2*255^2 = 137700 per row,
-// so up to 15595 rows fit below 2^31; accumulators are folded into residues
-// every KFOLD rows. The epilogue reduces sum_s A_s * (2^(8s) mod q) (< 2^62)
+// Bound: C_2 has the largest per-row sum, three full byte pairs, 3*255^2 =
+// 195075 (C_3: 2*255*15 + 2*255^2 = 137700), so up to 11008 rows fit below
+// 2^31; accumulators are folded into residues every KFOLD = 8192 rows. The epilogue reduces sum_s A_s * (2^(8s) mod q) (< 2^62)
 // with one Barrett reduction.
 //
 // Why legacy mma.sync: on sm_103a ptxas rejects tcgen05.mma .kind::i8, so the

@@ -1,4 +1,7 @@
-"""A CPU model of the tensor-core RowSel arithmetic, checked against the oracle.
+"""CPU models of the exact arithmetic of the tensor-core RowSel paths, checked
+against the oracle: the fused kernel (fp16 digits, 512-row fp32 groups), the
+two-pass kernel (256-row groups, magic-number conversion) and the INT8 path
+(unsigned byte limbs, int32 diagonal sums folded every 8192 rows).
 
 The tensor-core path (tcgen05 .kind::f16) rests on an exactness argument:
   - each residue x < 2^28 splits into balanced base-256 digits, byte u of
@@ -195,3 +198,71 @@ def test_two_pass_model_equals_oracle(shape):
     ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
     db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
     assert np.array_equal(tc_model_rowsel_two_pass(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
+
+
+# ---- the INT8 (mma.sync) path: unsigned byte limbs, int32 diagonal sums ----
+
+KFOLD = 8192                # rows per int32 accumulation in rowsel_imma.cu
+
+
+def byte_limbs(x):
+    x = np.asarray(x, dtype=np.int64)
+    return np.stack([(x >> (8 * u)) & 0xFF for u in range(4)], axis=-1)
+
+
+def test_imma_diagonal_bounds():
+    """Per-row maxima of C_s = sum_{u+v=s} x_u y_v with bytes <= 255 and a top
+    byte <= 15 (residues < 2^28): C_2 is the largest (3 * 255^2), so a fold
+    interval of 8192 rows keeps every int32 accumulator below 2^31."""
+    top = lambda u: 15 if u == 3 else 255
+    maxima = [sum(top(u) * top(s - u) for u in range(4) if 0 <= s - u < 4) for s in range(7)]
+    assert maxima == [65025, 130050, 195075, 137700, 72675, 7650, 225]
+    assert max(maxima) == maxima[2]
+    assert KFOLD * max(maxima) < 1 << 31 <= (KFOLD + 3000) * max(maxima)
+    # the epilogue's sum over the seven diagonals, each < 2^31, times 2^(8s) mod q < 2^28
+    assert 7 * (1 << 31) * (1 << 28) < 1 << 62
+
+
+def imma_model_rowsel(ct, db, primes, kfold=KFOLD):
+    """Byte limbs, seven diagonal int32 accumulators folded every `kfold` rows,
+    folded sums reduced as sum_s A_s (2^(8s) mod q)."""
+    ct = np.asarray(ct)
+    db = np.asarray(db)
+    B, D0, _, L, T = ct.shape
+    D1 = db.shape[1]
+    out = np.zeros((B, D1, 2, L, T), dtype=np.uint64)
+    for l, q in enumerate(primes):
+        q = int(q)
+        c = [pow(2, 8 * s, q) for s in range(7)]
+        for t in range(T):
+            a = byte_limbs(ct[:, :, :, l, t].transpose(0, 2, 1).reshape(2 * B, D0))
+            b = byte_limbs(db[:, :, l, t])
+            res = np.zeros((2 * B, D1), dtype=object)
+            for k0 in range(0, D0, kfold):
+                k1 = min(D0, k0 + kfold)
+                A = [sum(a[:, k0:k1, u] @ b[k0:k1, :, s - u] for u in range(4) if 0 <= s - u < 4) for s in range(7)]
+                for s in range(7):
+                    assert A[s].max() < 1 << 31
+                res = (res + sum(A[s].astype(object) * c[s] for s in range(7)) % q) % q
+            out[:, :, :, l, t] = res.astype(np.uint64).reshape(B, 2, D1).transpose(0, 2, 1)
+    return out.astype(np.uint32)
+
+
+@pytest.mark.parametrize("shape", [(2, 300, 4, 2, 2), (1, 70, 3, 1, 3)])
+def test_imma_model_equals_oracle(shape):
+    """Random residues, all q - 1, and residues whose three low bytes are all 255
+    (0x0EFFFFFF, the C_2 extreme, below both primes), with a small fold interval
+    so that several folds occur."""
+    B, D0, D1, L, T = shape
+    primes = PRIMES[:L]
+    ct = synth.uniform_residues(81 + D0, synth.TAG_CT, (B, D0, 2, L, T), primes, limb_axis=3)
+    db = synth.uniform_residues(82 + D0, synth.TAG_DB, (D0, D1, L, T), primes, limb_axis=2)
+    assert np.array_equal(imma_model_rowsel(ct, db, primes, kfold=64), oracle.rowsel(ct, db, primes))
+    for val in (None, 0x0EFFFFFF):
+        qm = np.array(primes, dtype=np.uint32)
+        fill_ct = qm[None, None, None, :, None] - 1 if val is None else np.uint32(val)
+        fill_db = qm[None, None, :, None] - 1 if val is None else np.uint32(val)
+        ct_w = np.broadcast_to(fill_ct, ct.shape).astype(np.uint32).copy()
+        db_w = np.broadcast_to(fill_db, db.shape).astype(np.uint32).copy()
+        assert np.all(ct_w < qm[None, None, None, :, None])
+        assert np.array_equal(imma_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
