@@ -1,7 +1,8 @@
-"""CPU models of the exact arithmetic of the tensor-core RowSel paths, checked
-against the oracle: the fused kernel (fp16 digits, 512-row fp32 groups), the
-two-pass kernel (256-row groups, magic-number conversion) and the INT8 path
-(unsigned byte limbs, int32 diagonal sums folded every 8192 rows).
+"""CPU models of the exact arithmetic of the RowSel paths, checked against the
+oracle: the tensor-core fused kernel (fp16 digits, 512-row fp32 groups), the
+two-pass kernel (256-row groups, magic-number conversion), the INT8 path
+(unsigned byte limbs, int32 diagonal sums folded every 8192 rows) and the
+CUDA-core path (64-bit sums reduced every 256 rows).
 
 The tensor-core path (tcgen05 .kind::f16) rests on an exactness argument:
   - each residue x < 2^28 splits into balanced base-256 digits, byte u of
@@ -266,3 +267,44 @@ def test_imma_model_equals_oracle(shape):
         db_w = np.broadcast_to(fill_db, db.shape).astype(np.uint32).copy()
         assert np.all(ct_w < qm[None, None, None, :, None])
         assert np.array_equal(imma_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
+
+
+# ---- the CUDA-core path: 64-bit sums, one Barrett reduction every 256 rows ----
+
+def test_cuda_core_accumulator_bound():
+    """A reduced residue (< q) plus 256 products of residues below q < 2^28 fits in
+    an unsigned 64-bit accumulator; 257 products of the largest residues would not."""
+    for q in list(PRIMES) + [(1 << 28) - 1]:
+        assert (q - 1) + 256 * (q - 1) ** 2 < 1 << 64
+    assert 257 * ((1 << 28) - 2) ** 2 >= 1 << 64
+
+
+def cc_model_rowsel(ct, db, primes, period=256):
+    """uint64 multiply-accumulate, reduced mod q every `period` rows and at the end."""
+    ct = np.asarray(ct, dtype=np.uint64)
+    db = np.asarray(db, dtype=np.uint64)
+    B, D0, _, L, T = ct.shape
+    out = np.zeros((B, db.shape[1], 2, L, T), dtype=np.uint64)
+    for l, q in enumerate(primes):
+        qq = np.uint64(q)
+        acc = np.zeros((B, db.shape[1], 2, T), dtype=np.uint64)
+        for k0 in range(0, D0, period):
+            for k in range(k0, min(D0, k0 + period)):
+                acc += ct[:, k, :, l, :][:, None, :, :] * db[k, :, l, :][None, :, None, :]
+            acc %= qq
+        out[:, :, :, l, :] = acc
+    return out.astype(np.uint32)
+
+
+def test_cuda_core_model_equals_oracle():
+    """All residues q - 1 over 600 rows (three reduction periods, the last ragged)
+    and random residues: the uint64 schedule equals the oracle."""
+    B, D0, D1, L, T = 2, 600, 3, 2, 3
+    primes = PRIMES
+    ct = synth.uniform_residues(91, synth.TAG_CT, (B, D0, 2, L, T), primes, limb_axis=3)
+    db = synth.uniform_residues(92, synth.TAG_DB, (D0, D1, L, T), primes, limb_axis=2)
+    assert np.array_equal(cc_model_rowsel(ct, db, primes), oracle.rowsel(ct, db, primes))
+    qm = np.array(primes, dtype=np.uint32)
+    ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
+    db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
+    assert np.array_equal(cc_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
