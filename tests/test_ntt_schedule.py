@@ -293,3 +293,31 @@ def test_offset_digits_match_the_oracle():
                  for i in range(ell)]
             assert d == oracle.balanced_digits(x, z, ell)
             assert all(abs(di) < min(primes) for di in d)
+
+
+def reduce64(x, q):
+    """The kernels' Barrett reduction: mu = floor(2^64 / q), qhat = high 64 bits
+    of x * mu, r = x - qhat q, one conditional subtraction."""
+    mu = ((1 << 64) - 1) // q
+    qhat = (x * mu) >> 64
+    r = x - qhat * q
+    assert 0 <= r < 2 * q            # the bound the single subtraction relies on
+    return r - q if r >= q else r
+
+
+def test_barrett_reduce64_any_64_bit_input():
+    rng = np.random.default_rng(5)
+    for q in list(synth.PRIMES_28) + [97, 193, (1 << 28) - 57]:
+        xs = [0, 1, q - 1, q, 2 * q - 1, (1 << 64) - 1, (1 << 64) - q, ((1 << 64) // q) * q,
+              ((1 << 64) // q) * q - 1] + [int(v) for v in rng.integers(0, 1 << 63, 2000, dtype=np.uint64)] + \
+             [int(v) << 1 | 1 for v in rng.integers(0, 1 << 63, 2000, dtype=np.uint64)]
+        for x in xs:
+            assert reduce64(x, q) == x % q
+
+
+def test_tree_accumulator_bounds():
+    """The trees' 64-bit multiply-accumulate: at most 2 ell <= 6 terms, each a lazy
+    forward-transform output (< 14q) times a key residue (< q); 14q < 2^32."""
+    for q in list(synth.PRIMES_28) + [(1 << 28) - 57]:
+        assert 14 * q < 1 << 32
+        assert 6 * (14 * q - 1) * (q - 1) < 1 << 63
