@@ -358,3 +358,11 @@ def test_debug_checks_reject_non_canonical_ciphertexts(g):
         g.gpir_set_debug(prev)
     h.rowsel(to_dev(bad), B, 1)              # off: accepted (the result is unspecified)
     h.close()
+
+
+@pytest.mark.parametrize("path", PATH_LIST)
+def test_largest_ring_degree(g, path):
+    """The largest ring degree the ABI accepts, N = 2^16, with the two largest
+    primes = 1 mod 2^17 below 2^28, two limbs, every path (the smallest, N = 4,
+    is in SHAPES)."""
+    _check_full(g, 3, 20, 9, 2, 65536, (268042241, 265420801), 500, PATHS[path])
