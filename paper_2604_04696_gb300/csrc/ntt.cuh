@@ -14,10 +14,11 @@
 // Arithmetic: Harvey's lazy butterflies ("Faster arithmetic for
 // number-theoretic transforms", J. Symb. Comp. 2014) with Shoup products:
 // a * w mod q for a fixed w is a*w - floor(a * w' / 2^32) * q with
-// w' = floor(w 2^32 / q), a value in [0, 2q) for any 32-bit a. Forward values
-// stay in [0, 4q), inverse values in [0, 2q); q < 2^28 keeps 4q < 2^32. A
-// conditional subtraction x >= c ? x - c : x is min(x, x - c) on unsigned
-// values.
+// w' = floor(w 2^32 / q), a value in [0, 2q) for any 32-bit a. Inverse values
+// stay in [0, 2q) (one conditional subtraction per butterfly). Forward values
+// are reduced below 8q once per radix round and grow by at most 2q per level,
+// so they stay below 14q; q < 2^28 keeps 14q < 2^32. A conditional
+// subtraction x >= c ? x - c : x is min(x, x - c) on unsigned values.
 //
 // GPU mapping. A polynomial of one limb belongs to a CTA of HALF threads
 // (the kernels run one CTA per limb of a tree node, the limbs of a node in one
