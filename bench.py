@@ -2,10 +2,17 @@
 
 One step = one batched RowSel (all of its work: every limb, slot, client and
 column) over device-resident synthetic inputs through the C ABI
-(gpir_rowsel_batch). Prints ONE JSON line (rank 0).
+(gpir_rowsel_batch). Prints ONE JSON line (rank 0). The default workload is
+the large database: N=4096, 2 limbs, D0=1024 x D1=128 (4 GiB in NTT form),
+128 clients.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--path auto|cudacore|imma|tc] [--impl gpir|reference]
+  python bench.py --case rowsel|coltor|expand|pir [--batch B --d0 D0 --d1 D1
+                  --n N --limbs L --path P --variant V --reps R ...]
+
+--case runs one seeded synthetic problem of any shape: a fixed launch sequence
+for profilers (ncu -k <kernel> -s <skip> -c <count>) and a quick timing.
 
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 (RowSel needs no exchange between replicas); value = all ranks' queries / the
@@ -63,26 +70,93 @@ def workload_shape(name, batch=None):
 # CPU oracle timing (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
-def time_oracle_sample(w, n_slots, seed=99):
-    import oracle
+def _sample_slots(w, n_slots, seed):
     rng = np.random.default_rng(seed)
-    slots = [(int(rng.integers(0, w["L"])), int(rng.integers(0, w["N"]))) for _ in range(n_slots)]
+    return [(int(rng.integers(0, w["L"])), int(rng.integers(0, w["N"]))) for _ in range(n_slots)]
+
+
+def _oracle_worker(w, slots):
+    """Generate the inputs of `slots` (untimed), then run the oracle on them;
+    returns (start, end) wall-clock stamps of the oracle part."""
+    import oracle
     ct = synth.ct_slots(w["seed"], w["B"], w["D0"], w["L"], w["N"], w["primes"], slots)
     db = synth.db_slots(w["seed"], w["D0"], w["D1"], w["L"], w["N"], w["primes"], slots)
-    t0 = time.perf_counter()
+    t0 = time.time()
     for k, (l, _t) in enumerate(slots):
         oracle.rowsel(ct[:, :, :, None, k:k + 1], db[:, :, None, k:k + 1], [w["primes"][l]])
-    return time.perf_counter() - t0
+    return t0, time.time()
 
 
-def oracle_queries_per_s(w, seconds_target=10.0):
-    """Time the oracle on a bounded sample of slots, extrapolate to the whole
-    batch (every limb and slot), return (queries/s, sample description)."""
-    t1 = time_oracle_sample(w, 1)
-    n = int(max(1, min(w["L"] * w["N"], seconds_target / max(t1, 1e-6))))
-    dt = time_oracle_sample(w, n, seed=7)
-    full = dt * (w["L"] * w["N"]) / n
-    return w["B"] / full, n, dt
+def host_cpu():
+    """(usable cores, CPU model) of this host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            model = "unknown"
+    return cores, model
+
+
+class OraclePool:
+    """The oracle, as it stands, run over slot subsets on every host core: one
+    spawned process per core (spawned, never forked from a CUDA process).
+    time(w, slots) returns the wall time of the parallel oracle section."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores) if cores > 1 else None
+
+    def time(self, w, slots):
+        if self.pool is None:
+            t0, t1 = _oracle_worker(w, slots)
+            return t1 - t0
+        chunks = [slots[k::self.cores] for k in range(self.cores)]
+        chunks = [c for c in chunks if c]
+        stamps = self.pool.starmap(_oracle_worker, [(w, c) for c in chunks])
+        return max(e for _s, e in stamps) - min(s for s, _e in stamps)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+
+def oracle_baseline(w, seconds_target=15.0):
+    """cpu_baseline: the oracle on all host cores over a bounded slot sample
+    (about `seconds_target` of wall time), plus a 1-core figure; both
+    extrapolated from the sample to the whole batch (every limb and slot)."""
+    cores, model = host_cpu()
+    t_one = OraclePool(1).time(w, _sample_slots(w, 1, 3))
+    total = w["L"] * w["N"]
+    n1 = int(max(1, min(total, 0.4 * seconds_target / max(t_one, 1e-6))))
+    dt1 = OraclePool(1).time(w, _sample_slots(w, n1, 5))
+    pool = OraclePool(cores)
+    try:
+        n = int(max(cores, min(total, cores * seconds_target / max(t_one, 1e-6))))
+        dt = pool.time(w, _sample_slots(w, n, 7))
+    finally:
+        pool.close()
+    return {"value": w["B"] / (dt * total / n), "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d (limb, slot) points on %d processes in %.1f s wall, extrapolated to the whole "
+                      "batch" % (n, total, cores, dt),
+            "one_core": {"value": w["B"] / (dt1 * total / n1), "unit": "queries/s",
+                         "sample": "%d points in %.1f s on 1 core, extrapolated" % (n1, dt1)},
+            "nproc": os.cpu_count(), "cpu_model": model}
 
 
 def run_reference(args):
@@ -91,24 +165,29 @@ def run_reference(args):
         return 0
     w = workload_shape(args.workload, args.batch)
     total_slots = w["L"] * w["N"]
-    # per step: a slot sample sized so warm-up + steps stay within ~2 minutes
-    t1 = time_oracle_sample(w, 1)
-    per_step_budget = 100.0 / max(1, args.steps + args.warmup)
-    n = int(max(1, min(total_slots, per_step_budget / max(t1, 1e-6))))
-    for _ in range(args.warmup):
-        time_oracle_sample(w, n, seed=1)
-    times = []
-    for s in range(args.steps):
-        times.append(time_oracle_sample(w, n, seed=100 + s))
+    cores, model = host_cpu()
+    t1 = OraclePool(1).time(w, _sample_slots(w, 1, 3))
+    # per step: a slot sample sized so warm-up + steps stay within ~2.5 minutes of wall time
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(max(cores, min(total_slots, cores * per_step_budget / max(t1, 1e-6))))
+    pool = OraclePool(cores)
+    try:
+        for k in range(args.warmup):
+            pool.time(w, _sample_slots(w, n, 1 + k))
+        times = [pool.time(w, _sample_slots(w, n, 100 + s)) for s in range(args.steps)]
+    finally:
+        pool.close()
     step = statistics.mean(times)
     qps = w["B"] / (step * total_slots / n)
-    sample = "%d of %d (limb, slot) points per step, extrapolated to the whole batch" % (n, total_slots)
+    sample = ("%d of %d (limb, slot) points per step on %d processes (one per host core), extrapolated to the whole "
+              "batch" % (n, total_slots, cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3 * total_slots / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (numpy)",
         "data": "synthetic", "config": cfg_dict(args.workload, w, "oracle", None),
-        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "nproc": os.cpu_count(), "cpu_model": model},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -500,7 +579,8 @@ def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
     one-hot selection drawn from a per-DB pool; p50/p99 latency and queries/s."""
-    from paper_2604_04696_gb300.server import Request, ResidentDb, Server, poisson_arrivals, toy_rlwe_query
+    from paper_2604_04696_gb300.server import Request, ResidentDb, Server, poisson_arrivals
+    from synth.device import toy_rlwe_query
     import gc
     gc.collect()
     torch.cuda.synchronize()
@@ -518,7 +598,8 @@ def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
         dbs.append(ResidentDb(h, D0, D1, N, L))
         pool = []
         for qi in range(4):
-            ct, _ = toy_rlwe_query(params, D0, L, N, primes, int(rng.integers(0, D0)), seed * 100 + k * 10 + qi)
+            ct, _ = toy_rlwe_query(g.gpir_fill_uniform, params, D0, L, N, primes, int(rng.integers(0, D0)),
+                                   seed * 100 + k * 10 + qi)
             pool.append(ct.cpu().pin_memory())
             del ct
         pools.append(pool)
@@ -545,23 +626,110 @@ def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     return out
 
 
+def run_case(a):
+    """One seeded synthetic problem through the C ABI: a fixed launch sequence
+    for profilers and a quick CUDA-event timing. Inputs are drawn on the device
+    with gpir_fill_uniform. rowsel: two fill kernels (DB, ciphertexts), the
+    upload's range check and packing kernels, then `reps` warm-up launches and
+    `reps` timed ones; the trees and the server step likewise."""
+    import torch
+    from paper_2604_04696_gb300 import _build
+    _build.build()
+    from paper_2604_04696_gb300 import gpir as g
+    B, D0, D1, N, L = (a.batch or 32), a.d0, a.d1, a.n, a.limbs
+    params = g.gpir_params_create(N, list(synth.PRIMES_28[:L]))
+    ell = g.gpir_coltor_gadget_digits(params)
+    ctw = 2 * L * N
+    dev = lambda n: torch.empty(n, dtype=torch.int32, device="cuda")
+    h = None
+    if a.case in ("rowsel", "pir"):
+        path = PATH_IDS[a.path] if a.path != "auto" else 4
+        db = dev(D0 * D1 * L * N)
+        g.gpir_fill_uniform(db, db.numel(), 0, 1, synth.TAG_DB, params, N)
+        h = g.gpir_db_upload(params, D0, D1, db, True, path if a.case == "rowsel" else g.GPIR_PATH_TC)
+        del db
+        torch.cuda.empty_cache()
+    if a.case == "rowsel":
+        ct = dev(B * D0 * ctw)
+        g.gpir_fill_uniform(ct, ct.numel(), 0, 1, synth.TAG_CT, params, N)
+        out = dev(B * D1 * ctw)
+        if a.variant >= 0:
+            g.gpir_set_variant(h, B, path, a.variant)
+        step = lambda: g.gpir_rowsel_batch(h, B, ct, out, path)
+        what = "rowsel %s B=%d D0=%d D1=%d N=%d L=%d" % (PATH_NAMES[path], B, D0, D1, N, L)
+    elif a.case == "coltor":
+        stages = D1.bit_length() - 1
+        ct = dev(B * D1 * ctw)
+        rgsw = dev(B * stages * 2 * ell * ctw)
+        out = dev(B * ctw)
+        g.gpir_fill_uniform(ct, ct.numel(), 0, 9, synth.TAG_COLTOR, params, N)
+        g.gpir_fill_uniform(rgsw, rgsw.numel(), 0, 9, synth.TAG_RGSW, params, N)
+        step = lambda: g.gpir_coltor(params, B, D1, ct, rgsw, out)
+        what = "coltor B=%d D1=%d N=%d L=%d ell=%d (%d stages)" % (B, D1, N, L, ell, stages)
+    elif a.case == "expand":
+        query = dev(B * ctw)
+        evk = dev(B * a.stages * ell * ctw)
+        out = dev(B * a.n_out * ctw)
+        g.gpir_fill_uniform(query, query.numel(), 0, 9, synth.TAG_QUERY, params, N)
+        g.gpir_fill_uniform(evk, evk.numel(), 0, 9, synth.TAG_EVK, params, N)
+        step = lambda: g.gpir_expand_query(params, B, a.stages, a.n_out, query, evk, out)
+        what = "expand B=%d J=%d n_out=%d N=%d L=%d ell=%d" % (B, a.stages, a.n_out, N, L, ell)
+    else:
+        J = (D0 - 1).bit_length()
+        stages = D1.bit_length() - 1
+        query = dev(B * ctw)
+        evk = dev(B * J * ell * ctw)
+        rgsw = dev(B * stages * 2 * ell * ctw)
+        g.gpir_fill_uniform(query, query.numel(), 0, 9, synth.TAG_QUERY, params, N)
+        g.gpir_fill_uniform(evk, evk.numel(), 0, 9, synth.TAG_EVK, params, N)
+        g.gpir_fill_uniform(rgsw, rgsw.numel(), 0, 9, synth.TAG_RGSW, params, N)
+        sel, rows, out = dev(B * D0 * ctw), dev(B * D1 * ctw), dev(B * ctw)
+        step = lambda: g.gpir_pir_batch(h, B, J, query, evk, rgsw, sel, rows, out, g.GPIR_PATH_TC)
+        what = "pir step B=%d D0=%d D1=%d N=%d L=%d (J=%d, %d ColTor stages)" % (B, D0, D1, N, L, J, stages)
+    for _ in range(a.reps):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    g.gpir_sync(None, 60000)
+    extra = ""
+    if a.case == "rowsel":
+        extra = " (variant %d)" % g.gpir_selected_variant(h, B, path)
+    print("%s%s: %.4f ms per call" % (what, extra, e0.elapsed_time(e1) / a.reps), flush=True)
+    if h is not None:
+        g.gpir_db_free(h)
+    g.gpir_params_destroy(params)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpir", choices=["gpir", "reference"])
-    ap.add_argument("--workload", default="c2_rowsel", choices=["c1_plain", "c2_rowsel", "c4_large", "c3_sweep"])
+    ap.add_argument("--workload", default="c4_large", choices=["c1_plain", "c2_rowsel", "c4_large", "c3_sweep"])
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--path", default="auto", choices=list(PATH_IDS))
-    ap.add_argument("--no-extras", action="store_true", help="skip path comparison, sweep and cpu baseline")
-    ap.add_argument("--peaks", action="store_true", help="build and run the peak-rate probe, then exit")
+    ap.add_argument("--no-extras", action="store_true", help="skip the sweep, trees, serving and pipeline sections")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--case", choices=["rowsel", "coltor", "expand", "pir"], default=None,
+                    help="run one synthetic problem (profiling / quick timing) and exit")
+    ap.add_argument("--d0", type=int, default=256)
+    ap.add_argument("--d1", type=int, default=64)
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--limbs", type=int, default=2)
+    ap.add_argument("--variant", type=int, default=-1, help="--case rowsel: tile variant (-1: library default)")
+    ap.add_argument("--stages", type=int, default=9, help="--case expand: expansion stages J")
+    ap.add_argument("--n-out", type=int, default=274, help="--case expand: outputs kept per client")
+    ap.add_argument("--reps", type=int, default=3, help="--case: warm-up and timed launches")
     args = ap.parse_args()
-    if args.peaks:
-        src = os.path.join(ROOT, "paper_2604_04696_gb300", "tools", "peaks_probe.cu")
-        exe = os.path.join(tempfile.gettempdir(), "gpir_peaks_probe")
-        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
-        return subprocess.run([exe]).returncode
+    if args.case:
+        return run_case(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
@@ -629,7 +797,10 @@ def main():
         "data": "synthetic", "config": cfg_dict(args.workload, w, PATH_NAMES[path], variant),
         "db_gbs": db_bytes / (ms / 1e3) / 1e9, "alg_gbs": alg / (ms / 1e3) / 1e9,
         "bit_exact_sample": exact,
-        "roofline": kernel_roofline(dom, w, ktimes[dom], peaks, args.workload),
+        # the dominant kernel's roofline: from the untraced step when the step is
+        # that one launch, else from its traced per-launch time
+        "roofline": kernel_roofline(dom, w, ms if (len(kcount) == 1 and kcount[dom] == 1) else ktimes[dom],
+                                    peaks, args.workload),
         "step_roofline": roofline(path, w, ms, peaks, args.workload),
         "kernels": {k: {"ms": v, "launches_per_step": kcount[k], "share": v * kcount[k] / sum(
             ktimes[x] * kcount[x] for x in ktimes)} for k, v in ktimes.items()},
@@ -642,7 +813,7 @@ def main():
     wl.close()
     if not args.no_extras and rank == 0:
         # queries/s vs batch on the same DB shape (best path), one line item per batch
-        if args.workload in ("c2_rowsel", "c3_sweep"):
+        if True:
             sweep = []
             for b in (1, 8, 32, 128, 256):
                 ws = workload_shape("c3_sweep", b)
@@ -655,18 +826,14 @@ def main():
                               "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
                 wk.close()
             line["sweep"] = sweep
-        if args.workload == "c2_rowsel":
-            line["pir_pipeline"] = run_pir_pipeline(g, torch)
+        line["pir_pipeline"] = run_pir_pipeline(g, torch)
         line["expand_query"] = run_expand(g, torch)
         line["coltor"] = run_coltor(g, torch)
         line["serving"] = {"workload": "c5_serving: 3 resident DBs 256x64 / 512x64 / 1024x128, N=4096, 2 limbs, "
                                        "Poisson arrivals, toy-RLWE one-hot queries, 3 streams, max batch 32",
                            "rates": run_serving(g, torch)}
-        if world == 1:
-            v, n, dt = oracle_queries_per_s(w, seconds_target=10.0)
-            line["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                                    "sample": "%d of %d (limb, slot) points in %.1f s, extrapolated"
-                                              % (n, w["L"] * w["N"], dt)}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(w, seconds_target=15.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

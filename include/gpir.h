@@ -62,6 +62,8 @@ extern "C" {
 #define GPIR_MAX_N      65536
 #define GPIR_MAX_PRIME_BITS 28   /* q < 2^28: every accumulator bound below
                                     is proven for this width               */
+#define GPIR_MAX_BATCH (1u << 30) /* clients per RowSel call (2*batch rows must
+                                    fit 32-bit row indices): GPIR_EINVAL above */
 
 typedef struct gpir_params gpir_params_t;
 typedef struct gpir_db gpir_db_t;
@@ -146,19 +148,27 @@ int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *st
  * once eagerly on `stream` (sizing workspaces; synchronizes), then captures
  * it; launch replays it on any stream. The job list (buffers, batch sizes)
  * is fixed at creation: refill the same ct buffers and replay. `stream` must
- * not be the legacy default stream. The graph's tensor-core workspace is the
- * one of the creating stream: do not replay it concurrently with other work
- * issued to that stream, or with another replay of the same graph. */
+ * not be the legacy default stream; create waits for the work already on it.
+ * Each graph owns its tensor-core workspace (allocated at create, outside the
+ * capture, freed by destroy), so later calls on any stream cannot disturb it;
+ * two replays of the SAME graph must not overlap (they share that workspace
+ * and the job's buffers). GPIR_ENOMEM if the workspace cannot be allocated. */
 typedef struct gpir_graph gpir_graph_t;
 int gpir_graph_create(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream,
                       gpir_graph_t **out);
 int gpir_graph_launch(gpir_graph_t *graph, void *stream);
 int gpir_graph_destroy(gpir_graph_t *graph);
 
-/* Wait for `stream` for at most timeout_ms milliseconds (0 = no limit).
- * GPIR_ETIMEOUT if the stream is still busy, or if a kernel of this library
- * reported that one of its bounded device-side waits expired; GPIR_ECUDA if
- * the stream reported an error. */
+/* Bounded synchronization (no counterpart in the paper; the library's own
+ * failure reporting): wait for `stream` for at most timeout_ms milliseconds
+ * (0 = no limit), then read and clear the device error word. GPIR_ETIMEOUT if
+ * the stream is still busy, or if a kernel of this library reported that one
+ * of its bounded device-side waits expired; GPIR_ECUDA if the stream reported
+ * an error. The error word is one per DEVICE, not per stream: an expiry
+ * raised by a kernel on another stream of the device is reported (and
+ * cleared) by whichever gpir_sync reads it first, and one still running on
+ * another stream is not seen yet. Callers that run several streams should
+ * sync after all of them have drained when they need the status of each. */
 int gpir_sync(void *stream, uint32_t timeout_ms);
 
 /* Debug checks (off by default; on when the environment variable GPIR_DEBUG
@@ -192,6 +202,15 @@ int gpir_selftest_bounded_wait(void *stream);
  * `*variant_out` (may be NULL) receives the chosen variant id. */
 int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                   uint32_t *out_dev, int path, void *stream, int *variant_out);
+
+/* Allocation-failure injection, for tests of the out-of-memory paths (no
+ * counterpart in the paper). With n > 0 the n-th device allocation the library
+ * makes from now on (1 = the next one) fails as if the device were out of
+ * memory -- the call that made it returns GPIR_ENOMEM and leaves its handle as
+ * it was -- and the injection then disarms itself; n <= 0 disarms it. The
+ * environment variable GPIR_FAIL_ALLOC=n arms it when the library first
+ * allocates. Returns the previous countdown (0 = off). Host-only. */
+long gpir_set_fail_alloc(long n);
 
 /* Number of kernel variants compiled for `path` and the id in use for a
  * shape (-1 if none chosen yet). Host-only. */

@@ -319,7 +319,7 @@ int get_workspace(int dev, cudaStream_t s, size_t words, uint32_t **out) {
       w.first = nullptr;
       w.second = 0;
     }
-    cudaError_t e = cudaMalloc(&w.first, words * 4);
+    cudaError_t e = dev_malloc(reinterpret_cast<void **>(&w.first), words * 4);
     if (e != cudaSuccess) {
       w.first = nullptr;
       return set_cuda_error(e);

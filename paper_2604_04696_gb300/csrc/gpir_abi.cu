@@ -32,6 +32,37 @@ int set_cuda_error(cudaError_t e) {
   return GPIR_ECUDA;
 }
 
+// Allocation-failure injection, for tests of the GPIR_ENOMEM paths that
+// exhaust no GPU: armed with n > 0, the n-th device allocation the library
+// makes from then on fails as if the device were out of memory, and the
+// injection disarms itself. Armed from the environment variable
+// GPIR_FAIL_ALLOC when the library first allocates, or by gpir_set_fail_alloc.
+static std::atomic<long> g_fail_alloc{-1};   // -1: environment not read yet, 0: off
+
+static void fail_alloc_init() {
+  if (g_fail_alloc.load() >= 0) return;
+  const char *v = std::getenv("GPIR_FAIL_ALLOC");
+  long n = v ? std::strtol(v, nullptr, 10) : 0;
+  long expect = -1;
+  g_fail_alloc.compare_exchange_strong(expect, n > 0 ? n : 0);
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  fail_alloc_init();
+  for (;;) {
+    long v = g_fail_alloc.load();
+    if (v <= 0) break;
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) {
+      if (v == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 unsigned int *device_error_word() {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -318,9 +349,9 @@ int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1, const 
   db->variants = new std::map<std::pair<int, uint32_t>, int>();
   db->mu = new std::mutex();
   int rc = GPIR_OK;
-  unsigned int *bad = nullptr;
-  cudaError_t e = cudaMalloc(&db->db_pmajor, bytes);
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&db->db_pmajor), bytes);
   if (e != cudaSuccess) {
+    db->db_pmajor = nullptr;
     rc = set_cuda_error(e);
     goto fail;
   }
@@ -330,29 +361,10 @@ int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1, const 
     rc = set_cuda_error(e);
     goto fail;
   }
-  e = cudaMallocAsync(&bad, sizeof(unsigned int), s);
-  if (e != cudaSuccess) {
-    rc = set_cuda_error(e);
-    goto fail;
-  }
-  cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
-  range_check_kernel<<<sm_count() * 4, 256, 0, s>>>(db->db_pmajor, count, params->n, params->num_limbs,
-                                                     params->limbs, bad);
-  {
-    unsigned int hbad = 0;
-    e = cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFreeAsync(bad, s);
-    bad = nullptr;
-    if (e != cudaSuccess) {
-      rc = set_cuda_error(e);
-      goto fail;
-    }
-    if (hbad) {
-      rc = GPIR_ERANGE;
-      goto fail;
-    }
-  }
+  // every residue below its limb's prime ([D0][D1] polynomials of [L][N]);
+  // synchronizes s, allocates nothing
+  rc = check_residues_dev(params[0], db->db_pmajor, count, s);
+  if (rc != GPIR_OK) goto fail;
   if (path_mask & GPIR_PATH_TC) {
     rc = rowsel_tc_prepare(db, s);
     if (rc != GPIR_OK) goto fail;
@@ -385,7 +397,7 @@ size_t gpir_db_device_bytes(const gpir_db_t *db) {
 int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
                       void *stream) {
   NvtxRange nvtx("gpir_rowsel_batch");
-  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  if (!db || !ct_dev || !out_dev || batch == 0 || batch > GPIR_MAX_BATCH) return GPIR_EINVAL;
   int p = resolve_path(db, path, batch);
   if (p == -1) return GPIR_EINVAL;
   if (p == -2) return GPIR_ENOTSUP;
@@ -405,7 +417,7 @@ int gpir_pir_batch(const gpir_db_t *db, uint32_t batch, uint32_t stages, const u
                    const uint32_t *evk_dev, const uint32_t *rgsw_dev, uint32_t *sel_dev, uint32_t *rows_dev,
                    uint32_t *out_dev, int path, void *stream) {
   NvtxRange nvtx("gpir_pir_batch");
-  if (!db || batch == 0 || !query_dev || !rgsw_dev || !sel_dev || !rows_dev || !out_dev) return GPIR_EINVAL;
+  if (!db || batch == 0 || batch > GPIR_MAX_BATCH || !query_dev || !rgsw_dev || !sel_dev || !rows_dev || !out_dev) return GPIR_EINVAL;
   if (db->d1 < 2 || (db->d1 & (db->d1 - 1)) != 0) return GPIR_EINVAL;
   if (stages >= 32 || db->d0 > (1u << stages)) return GPIR_EINVAL;
   const size_t ctw = (size_t)2 * db->params.num_limbs * db->params.n * 4;
@@ -456,7 +468,7 @@ int host_pipe(int dev, HostPipe **out) {
 int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t *ct_host, uint32_t *out_host,
                            int path, void *stream) {
   NvtxRange nvtx("gpir_rowsel_batch_host");
-  if (!db_c || !ct_host || !out_host || batch == 0) return GPIR_EINVAL;
+  if (!db_c || !ct_host || !out_host || batch == 0 || batch > GPIR_MAX_BATCH) return GPIR_EINVAL;
   gpir_db *db = const_cast<gpir_db *>(db_c);
   if (debug_checks()) {
     // the host buffer, on the CPU: residue i belongs to limb (i / N) % L
@@ -477,8 +489,11 @@ int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t
     }
     db->ws_ct = nullptr;
     db->ws_ct_bytes = 0;
-    e = cudaMalloc(&db->ws_ct, ct_bytes);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    e = dev_malloc(reinterpret_cast<void **>(&db->ws_ct), ct_bytes);
+    if (e != cudaSuccess) {
+      db->ws_ct = nullptr;
+      return set_cuda_error(e);
+    }
     db->ws_ct_bytes = ct_bytes;
   }
   if (db->ws_out_bytes < out_bytes) {
@@ -488,8 +503,11 @@ int gpir_rowsel_batch_host(const gpir_db_t *db_c, uint32_t batch, const uint32_t
     }
     db->ws_out = nullptr;
     db->ws_out_bytes = 0;
-    e = cudaMalloc(&db->ws_out, out_bytes);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    e = dev_malloc(reinterpret_cast<void **>(&db->ws_out), out_bytes);
+    if (e != cudaSuccess) {
+      db->ws_out = nullptr;
+      return set_cuda_error(e);
+    }
     db->ws_out_bytes = out_bytes;
   }
   // Small batches: one copy in, RowSel, one copy out, all on `stream`.
@@ -548,10 +566,25 @@ int gpir_rowsel_multi(const gpir_job_t *jobs, uint32_t njobs, int path, void *st
   NvtxRange nvtx("gpir_rowsel_multi");
   if (!jobs || njobs == 0) return GPIR_EINVAL;
   for (uint32_t k = 0; k < njobs; ++k) {
-    if (!jobs[k].db || !jobs[k].ct || !jobs[k].out || jobs[k].batch == 0) return GPIR_EINVAL;
+    if (!jobs[k].db || !jobs[k].ct || !jobs[k].out || jobs[k].batch == 0 || jobs[k].batch > GPIR_MAX_BATCH)
+      return GPIR_EINVAL;
     const gpir_params &a = jobs[0].db->params, &b = jobs[k].db->params;
     if (a.n != b.n || a.num_limbs != b.num_limbs || memcmp(a.primes, b.primes, sizeof(a.primes)) != 0)
       return GPIR_EINVAL;
+    if (((uintptr_t)jobs[k].ct & 15u) || ((uintptr_t)jobs[k].out & 15u)) return GPIR_EINVAL;
+  }
+  // no output may overlap any ciphertext or output buffer of the call
+  for (uint32_t k = 0; k < njobs; ++k) {
+    const gpir_params &prm = jobs[k].db->params;
+    const size_t poly = (size_t)2 * prm.num_limbs * prm.n * 4;
+    const uintptr_t o0 = (uintptr_t)jobs[k].out, o1 = o0 + (size_t)jobs[k].batch * jobs[k].db->d1 * poly;
+    for (uint32_t k2 = 0; k2 < njobs; ++k2) {
+      const uintptr_t c0 = (uintptr_t)jobs[k2].ct, c1 = c0 + (size_t)jobs[k2].batch * jobs[k2].db->d0 * poly;
+      if (c0 < o1 && o0 < c1) return GPIR_EINVAL;
+      if (k2 == k) continue;
+      const uintptr_t p0 = (uintptr_t)jobs[k2].out, p1 = p0 + (size_t)jobs[k2].batch * jobs[k2].db->d1 * poly;
+      if (p0 < o1 && o0 < p1) return GPIR_EINVAL;
+    }
   }
   if (debug_checks())
     for (uint32_t k = 0; k < njobs; ++k) {
@@ -601,6 +634,11 @@ int gpir_set_debug(int on) {
   return prev;
 }
 
+long gpir_set_fail_alloc(long n) {
+  fail_alloc_init();
+  return g_fail_alloc.exchange(n > 0 ? n : 0);
+}
+
 int gpir_num_variants(int path) { return num_variants(path); }
 
 int gpir_selected_variant(const gpir_db_t *db, uint32_t batch, int path) {
@@ -619,7 +657,7 @@ int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant)
 
 int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,
                   void *stream, int *variant_out) {
-  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  if (!db || !ct_dev || !out_dev || batch == 0 || batch > GPIR_MAX_BATCH) return GPIR_EINVAL;
   int paths[3], np = 0;
   if (path == GPIR_PATH_AUTO) {
     for (int p : {GPIR_PATH_CUDACORE, GPIR_PATH_IMMA, GPIR_PATH_TC})

@@ -64,6 +64,11 @@ namespace gpir {
 // Error helpers
 int set_cuda_error(cudaError_t e);
 
+// Every device allocation of the library goes through this wrapper: cudaMalloc,
+// unless the allocation-failure injection (GPIR_FAIL_ALLOC /
+// gpir_set_fail_alloc) makes it fail with cudaErrorMemoryAllocation.
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 // TMA descriptor encoding (driver entry point resolved at first use).
 int encode_tiled_u32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
                      const uint64_t *strides_bytes /* rank-1 entries */, const uint32_t *box);
@@ -113,6 +118,8 @@ bool trace_enabled();
 void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 
 int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
+// Free the tensor-core workspace kept for (current device, stream), if any.
+void rowsel_tc_release_stream(cudaStream_t stream);
 size_t rowsel_tc_multi_workspace(const gpir_job_t *jobs, uint32_t njobs);
 
 int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaStream_t stream);

@@ -141,7 +141,7 @@ int ring_tables(const gpir_params_t *params, ntt::Ring *out) {
   R.offset = 0;
   for (uint32_t k = 0; k + 1 < R.ell; ++k) R.offset += (1ull << (ntt::LOG_BASE - 1)) << (ntt::LOG_BASE * k);
   uint2 *mem = nullptr;
-  e = cudaMalloc(&mem, host.size() * sizeof(uint2));
+  e = dev_malloc(reinterpret_cast<void **>(&mem), host.size() * sizeof(uint2));
   if (e != cudaSuccess) return set_cuda_error(e);
   e = cudaMemcpy(mem, host.data(), host.size() * sizeof(uint2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {

@@ -35,45 +35,83 @@ int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaSt
 
 }  // namespace gpir
 
+// A graph owns a private stream: the eager run and the capture both issue on
+// it, so the tensor-core workspace the captured kernels address is the one
+// kept for that stream, which no other call uses and which lives until
+// gpir_graph_destroy. Later calls on the caller's streams (say a larger batch
+// that grows their workspaces) cannot free memory the graph replays into.
 struct gpir_graph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  cudaStream_t own;
 };
 
 using namespace gpir;
+
+namespace {
+void graph_free(gpir_graph *g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->own) {
+    rowsel_tc_release_stream(g->own);
+    cudaStreamDestroy(g->own);
+  }
+  delete g;
+}
+}  // namespace
 
 extern "C" {
 
 int gpir_graph_create(const gpir_job_t *jobs, uint32_t njobs, int path, void *stream, gpir_graph_t **out) {
   if (!jobs || njobs == 0 || !out || !stream) return GPIR_EINVAL;
   *out = nullptr;
-  cudaStream_t s = (cudaStream_t)stream;
-  // One eager run sizes every workspace outside the capture (and checks the
-  // arguments); its results are overwritten by every replay.
-  int rc = gpir_rowsel_multi(jobs, njobs, path, stream);
-  if (rc != GPIR_OK) return rc;
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return set_cuda_error(e);
   gpir_graph *g = new (std::nothrow) gpir_graph;
   if (!g) return GPIR_ENOMEM;
   g->graph = nullptr;
   g->exec = nullptr;
-  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  g->own = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->own, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
-    delete g;
+    g->own = nullptr;
+    graph_free(g);
     return set_cuda_error(e);
   }
-  rc = gpir_rowsel_multi(jobs, njobs, path, stream);
-  e = cudaStreamEndCapture(s, &g->graph);
+  // The eager run sees everything already enqueued on the caller's stream
+  // (say the fill of its ciphertext buffers), sizes the graph's own workspace
+  // outside the capture and checks the arguments; replays overwrite its results.
+  cudaEvent_t ready = nullptr;
+  e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->own, ready, 0);
+  if (ready) cudaEventDestroy(ready);
+  if (e != cudaSuccess) {
+    graph_free(g);
+    return set_cuda_error(e);
+  }
+  int rc = gpir_rowsel_multi(jobs, njobs, path, g->own);
+  if (rc == GPIR_OK) {
+    e = cudaStreamSynchronize(g->own);
+    if (e != cudaSuccess) rc = set_cuda_error(e);
+  }
+  if (rc != GPIR_OK) {
+    graph_free(g);
+    return rc;
+  }
+  e = cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    graph_free(g);
+    return set_cuda_error(e);
+  }
+  rc = gpir_rowsel_multi(jobs, njobs, path, g->own);
+  e = cudaStreamEndCapture(g->own, &g->graph);
   if (rc != GPIR_OK || e != cudaSuccess) {
-    if (g->graph) cudaGraphDestroy(g->graph);
-    delete g;
+    graph_free(g);
     return rc != GPIR_OK ? rc : set_cuda_error(e);
   }
   e = cudaGraphInstantiate(&g->exec, g->graph, 0);
   if (e != cudaSuccess) {
-    cudaGraphDestroy(g->graph);
-    delete g;
+    g->exec = nullptr;
+    graph_free(g);
     return set_cuda_error(e);
   }
   *out = g;
@@ -88,9 +126,7 @@ int gpir_graph_launch(gpir_graph_t *g, void *stream) {
 
 int gpir_graph_destroy(gpir_graph_t *g) {
   if (!g) return GPIR_OK;
-  if (g->exec) cudaGraphExecDestroy(g->exec);
-  if (g->graph) cudaGraphDestroy(g->graph);
-  delete g;
+  graph_free(g);
   return GPIR_OK;
 }
 

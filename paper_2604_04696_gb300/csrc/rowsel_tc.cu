@@ -1903,7 +1903,7 @@ int rowsel_tc_prepare(gpir_db *db, cudaStream_t stream) {
   const uint32_t nblk = (db->d1 + NCOLS - 1) / NCOLS, kch = (db->d0 + KCHUNK - 1) / KCHUNK;
   const uint64_t slots = (uint64_t)L * N;
   const size_t bytes = (size_t)slots * nblk * kch * B_TILE_BYTES;
-  cudaError_t e = cudaMalloc(&db->db_digits, bytes);
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&db->db_digits), bytes);
   if (e != cudaSuccess) {
     db->db_digits = nullptr;
     return set_cuda_error(e);
@@ -2066,13 +2066,33 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
     }
     w.ptr = nullptr;
     w.bytes = 0;
-    e = cudaMalloc(&w.ptr, need);
-    if (e != cudaSuccess) return set_cuda_error(e);
+    e = dev_malloc(&w.ptr, need);
+    if (e != cudaSuccess) {
+      w.ptr = nullptr;
+      return set_cuda_error(e);
+    }
     w.bytes = need;
   }
   *out = reinterpret_cast<uint8_t *>(w.ptr);
   return GPIR_OK;
 }
+
+}  // namespace
+
+void rowsel_tc_release_stream(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto it = g_ws.find({dev, stream});
+  if (it == g_ws.end()) return;
+  if (it->second.ptr) {
+    cudaStreamSynchronize(stream);
+    cudaFree(it->second.ptr);
+  }
+  g_ws.erase(it);
+}
+
+namespace {
 
 // Fused-kernel tile variants: digit-ring size (against the 129 MB L2) and L2
 // eviction hints; the autotuner picks one per shape.
@@ -2447,7 +2467,7 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
                                          uint32_t *out_dev, void *stream) {
   using namespace gpir;
   NvtxRange nvtx("gpir_rowsel_batch_noalloc");
-  if (!db || !ct_dev || !out_dev || batch == 0) return GPIR_EINVAL;
+  if (!db || !ct_dev || !out_dev || batch == 0 || batch > GPIR_MAX_BATCH) return GPIR_EINVAL;
   if (!(db->path_mask & GPIR_PATH_TC) || !db->db_digits) return GPIR_ENOTSUP;
   const uint32_t L = db->params.num_limbs, N = db->params.n, M = 2 * batch;
   const uint64_t slots = (uint64_t)L * N;
@@ -2455,6 +2475,7 @@ extern "C" int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, co
   const size_t out_bytes = (size_t)batch * db->d1 * 2 * slots * 4;
   const uintptr_t a0 = (uintptr_t)ct_dev, a1 = a0 + ct_bytes, b0 = (uintptr_t)out_dev, b1 = b0 + out_bytes;
   if (a0 < b1 && b0 < a1) return GPIR_EINVAL;
+  if ((a0 & 15u) || (b0 & 15u)) return GPIR_EINVAL;
   const uint32_t mblk = (M + MROWS - 1) / MROWS;
   const uint32_t kch = (db->d0 + KCHUNK - 1) / KCHUNK;
   const uint64_t a_bytes = slots * mblk * kch * (uint64_t)A_TILE_BYTES;

@@ -32,6 +32,7 @@ GPIR_MAX_LIMBS = 8
 GPIR_MIN_N = 4
 GPIR_MAX_N = 65536
 GPIR_MAX_PRIME_BITS = 28
+GPIR_MAX_BATCH = 1 << 30
 
 
 class GpirError(RuntimeError):
@@ -75,6 +76,7 @@ def _load():
         "gpir_sync": (I, [P, U32]),
         "gpir_selftest_bounded_wait": (I, [P]),
         "gpir_set_debug": (I, [I]),
+        "gpir_set_fail_alloc": (ctypes.c_long, [ctypes.c_long]),
         "gpir_autotune": (I, [P, U32, P, P, I, P, ctypes.POINTER(I)]),
         "gpir_num_variants": (I, [I]),
         "gpir_selected_variant": (I, [P, U32, I]),
@@ -212,6 +214,12 @@ def gpir_sync(stream=None, timeout_ms=0):
 def gpir_set_debug(on=True):
     """Debug checks of the ciphertext residues on or off; returns the previous setting."""
     return lib.gpir_set_debug(1 if on else 0)
+
+
+def gpir_set_fail_alloc(n):
+    """Arm (n > 0: the n-th device allocation from now fails) or disarm (n <= 0)
+    the allocation-failure injection; returns the previous countdown."""
+    return lib.gpir_set_fail_alloc(int(n))
 
 
 def gpir_selftest_bounded_wait(stream=None):

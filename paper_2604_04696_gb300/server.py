@@ -181,34 +181,3 @@ def poisson_arrivals(rate_qps, count, seed):
     """Arrival times (s) of a Poisson process: seeded exponential gaps."""
     rng = np.random.default_rng(seed)
     return np.cumsum(rng.exponential(1.0 / rate_qps, size=count))
-
-
-def toy_rlwe_query(params_ptr, D0, L, N, primes, istar, seed, stream=None):
-    """Noiseless toy RLWE one-hot query in the NTT domain, made on the device:
-    ct_i = (a_i, a_i (.) s + [i == istar]) mod q_l with a_i, s uniform (the
-    NTT of the constant 1 is all ones). Returns (ct [D0][2][L][N] int32 on the
-    device, s [L][N] int64 on the device). Client-side query encoding, used to
-    drive and check the server; not part of RowSel."""
-    import synth
-    a = torch.empty(D0 * L * N, dtype=torch.int32, device="cuda")
-    s = torch.empty(L * N, dtype=torch.int32, device="cuda")
-    g.gpir_fill_uniform(a, a.numel(), 0, seed, synth.TAG_MASK, params_ptr, N, stream)
-    g.gpir_fill_uniform(s, s.numel(), 0, seed, synth.TAG_SECRET, params_ptr, N, stream)
-    a = a.view(D0, L, N).long()
-    s = s.view(L, N).long()
-    q = torch.tensor(list(primes), dtype=torch.int64, device="cuda").view(1, L, 1)
-    b = (a * s.unsqueeze(0)) % q
-    b[istar] = (b[istar] + 1) % q[0]
-    ct = torch.stack([a, b], dim=1).to(torch.int32).contiguous()
-    return ct, s
-
-
-def decrypt_check(out, s, db_row, primes):
-    """out: [D1][2][L][N] int32 (device), s: [L][N] int64, db_row: [D1][L][N] int32.
-    True iff b - a (.) s == DB[i*][j] for every j (noiseless toy RLWE)."""
-    L = s.shape[0]
-    q = torch.tensor(list(primes), dtype=torch.int64, device=out.device).view(1, L, 1)
-    a = out[:, 0].long()
-    b = out[:, 1].long()
-    m = (b - (a * s.unsqueeze(0)) % q) % q
-    return bool(torch.equal(m, db_row.long()))

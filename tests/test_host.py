@@ -1,6 +1,7 @@
 """Host-side logic without a GPU: sizes, the input generator, the C ABI's
 exported symbols and its argument checks."""
 
+import ctypes
 import json
 import os
 import re
@@ -196,3 +197,50 @@ def test_debug_switch_and_environment():
     env["GPIR_DEBUG"] = "1"
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
     assert r.stdout.split() == ["1", "1", "0"]
+
+
+def test_batch_limit_rejected_before_any_dereference(g):
+    """A batch above GPIR_MAX_BATCH (2 * batch rows would not fit 32-bit row
+    indices) is an argument error in every RowSel entry point, found before
+    the handle is touched (the fake handle address here is never read)."""
+    big = g.GPIR_MAX_BATCH + 1
+    fake_db, A, B = 1 << 40, 2 << 40, 3 << 40
+    assert g.lib.gpir_rowsel_batch(fake_db, big, A, B, 0, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_rowsel_batch_host(fake_db, big, A, B, 0, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_rowsel_batch_noalloc(fake_db, big, A, B, None) == g.GPIR_EINVAL
+    assert g.lib.gpir_autotune(fake_db, big, A, B, 0, None, None) == g.GPIR_EINVAL
+    job = g.gpir_job_t(fake_db, big, 0, A, B)
+    assert g.lib.gpir_rowsel_multi(ctypes.pointer(job), 1, 0, None) == g.GPIR_EINVAL
+
+
+def test_fail_alloc_injection_on_the_host():
+    """The allocation-failure hook: GPIR_FAIL_ALLOC=n in the environment (or
+    gpir_set_fail_alloc) makes the n-th device allocation fail with
+    GPIR_ENOMEM, then disarms. Here (no GPU) the database upload's first
+    allocation is the one counted: armed at 1 it returns GPIR_ENOMEM; disarmed,
+    the same call reaches the CUDA runtime and fails otherwise."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, synth\n"
+        "from paper_2604_04696_gb300 import gpir as g\n"
+        "P = g.gpir_params_create(16, list(synth.PRIMES_28))\n"
+        "db = np.zeros(2 * 2 * 2 * 16, dtype=np.uint32)\n"
+        "def up():\n"
+        "    import ctypes\n"
+        "    h = ctypes.c_void_p()\n"
+        "    return g.lib.gpir_db_upload(P, 2, 2, db.ctypes.data, 0, 1, None, ctypes.byref(h))\n"
+        "first = up()\n"                       # env armed at 1: this one fails
+        "second = up()\n"                      # disarmed
+        "prev = g.gpir_set_fail_alloc(2)\n"
+        "third = up()\n"                       # countdown 2 -> 1: real allocation attempt
+        "fourth = up()\n"                      # the 2nd one: injected
+        "fifth = up()\n"
+        "print(first, second, prev, third, fourth, fifth, g.gpir_set_fail_alloc(0))\n")
+    env = dict(os.environ)
+    env["GPIR_FAIL_ALLOC"] = "1"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    first, second, prev, third, fourth, fifth, last = [int(x) for x in r.stdout.split()]
+    ENOMEM = -3
+    assert first == ENOMEM and prev == 0 and fourth == ENOMEM and last == 0
+    assert second != ENOMEM and third != ENOMEM and fifth != ENOMEM

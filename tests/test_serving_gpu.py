@@ -18,7 +18,8 @@ def g():
 
 def _setup(g, shapes, N, primes, seed):
     import torch
-    from paper_2604_04696_gb300.server import ResidentDb, toy_rlwe_query
+    from paper_2604_04696_gb300.server import ResidentDb
+    from synth.device import toy_rlwe_query
     params = g.gpir_params_create(N, list(primes))
     L = len(primes)
     dbs, db_dev, pools = [], [], []
@@ -30,7 +31,8 @@ def _setup(g, shapes, N, primes, seed):
         db_dev.append(db.view(D0, D1, L, N))
         pool = []
         for qi, istar in enumerate(sorted({0, D0 - 1, D0 // 2})):
-            ct, sec = toy_rlwe_query(params, D0, L, N, primes, istar, seed * 100 + k * 10 + qi)
+            ct, sec = toy_rlwe_query(g.gpir_fill_uniform, params, D0, L, N, primes, istar,
+                                     seed * 100 + k * 10 + qi)
             pool.append((istar, ct, ct.cpu().pin_memory(), sec))
         pools.append(pool)
     torch.cuda.synchronize()
@@ -39,7 +41,7 @@ def _setup(g, shapes, N, primes, seed):
 
 def test_served_answers_equal_alone_and_decrypt(g):
     import torch
-    from paper_2604_04696_gb300.server import Request, Server, poisson_arrivals, decrypt_check
+    from paper_2604_04696_gb300.server import Request, Server, poisson_arrivals
     N, primes = 256, synth.PRIMES_28
     shapes = [(40, 24), (70, 64), (33, 130)]
     params, dbs, db_dev, pools = _setup(g, shapes, N, primes, 40)
@@ -92,3 +94,15 @@ def test_admission_budget_and_rejection(g):
         for d in dbs:
             g.gpir_db_free(d.h)
         g.gpir_params_destroy(params)
+
+
+def decrypt_check(out, s, db_row, primes):
+    """out: [D1][2][L][N] int32 (device), s: [L][N] int64, db_row: [D1][L][N] int32.
+    True iff b - a (.) s == DB[i*][j] for every j (noiseless toy RLWE)."""
+    import torch
+    L = s.shape[0]
+    q = torch.tensor(list(primes), dtype=torch.int64, device=out.device).view(1, L, 1)
+    a = out[:, 0].long()
+    b = out[:, 1].long()
+    m = (b - (a * s.unsqueeze(0)) % q) % q
+    return bool(torch.equal(m, db_row.long()))
