@@ -333,19 +333,35 @@ def roofline(path_id, w, ms, peaks, workload):
 
 
 class GpuWorkload:
-    def __init__(self, g, torch, w, path_mask):
-        self.g, self.torch, self.w = g, torch, w
+    """One RowSel workload on this GPU: the database made resident and one
+    batch of selection ciphertexts, all drawn on the device. With `shard` (a
+    SlotShard) only that rank's slots are kept: the full tensors are drawn,
+    sliced to the shard's compact [..., L, T] layout and dropped, so every rank
+    holds exactly the values of the unsharded workload at its slots."""
+
+    def __init__(self, g, torch, w, path_mask, shard=None):
+        self.g, self.torch, self.w, self.shard = g, torch, w, shard
         N, L, D0, D1, B = w["N"], w["L"], w["D0"], w["D1"], w["B"]
-        self.params = g.gpir_params_create(N, w["primes"])
+        T = shard.T if shard else N
+        self.T = T
+        gen = g.gpir_params_create(N, w["primes"])              # the full ring: generator limb mapping
+        self.params = g.gpir_params_create(T, w["primes"]) if shard else gen
         self.stream = torch.cuda.current_stream()
         db = torch.empty(D0 * D1 * L * N, dtype=torch.int32, device="cuda")
-        g.gpir_fill_uniform(db, db.numel(), 0, w["seed"], synth.TAG_DB, self.params, N, self.stream)
+        g.gpir_fill_uniform(db, db.numel(), 0, w["seed"], synth.TAG_DB, gen, N, self.stream)
+        if shard:
+            db = shard.take(db.view(D0, D1, L, N))
         self.h = g.gpir_db_upload(self.params, D0, D1, db, True, path_mask, self.stream)
         del db
-        self.ct = torch.empty(B * D0 * 2 * L * N, dtype=torch.int32, device="cuda")
-        g.gpir_fill_uniform(self.ct, self.ct.numel(), 0, w["seed"], synth.TAG_CT, self.params, N, self.stream)
-        self.out = torch.empty(B * D1 * 2 * L * N, dtype=torch.int32, device="cuda")
+        ct = torch.empty(B * D0 * 2 * L * N, dtype=torch.int32, device="cuda")
+        g.gpir_fill_uniform(ct, ct.numel(), 0, w["seed"], synth.TAG_CT, gen, N, self.stream)
+        self.ct = shard.take(ct.view(B, D0, 2, L, N)).view(-1) if shard else ct
+        del ct
+        self.out = torch.empty(B * D1 * 2 * L * T, dtype=torch.int32, device="cuda")
+        if shard:
+            g.gpir_params_destroy(gen)
         torch.cuda.synchronize()
+        torch.cuda.empty_cache()
 
     def step(self, path):
         self.g.gpir_rowsel_batch(self.h, self.w["B"], self.ct, self.out, path, self.stream)
@@ -374,15 +390,18 @@ class GpuWorkload:
         return e0.elapsed_time(e1) / steps, clk
 
     def check_sample(self, n_slots=3):
-        """Bit-exact check of a few sampled (limb, slot) points against the oracle."""
+        """Bit-exact check of a few sampled (limb, slot) points of this GPU's
+        slots against the oracle."""
         import oracle
         w = self.w
+        t0 = self.shard.t0 if self.shard else 0
         rng = np.random.default_rng(5)
-        slots = [(int(rng.integers(0, w["L"])), int(rng.integers(0, w["N"]))) for _ in range(n_slots)]
+        local = [(int(rng.integers(0, w["L"])), int(rng.integers(0, self.T))) for _ in range(n_slots)]
+        slots = [(l, t0 + t) for l, t in local]
         ct = synth.ct_slots(w["seed"], w["B"], w["D0"], w["L"], w["N"], w["primes"], slots)
         db = synth.db_slots(w["seed"], w["D0"], w["D1"], w["L"], w["N"], w["primes"], slots)
-        out = self.out.view(w["B"], w["D1"], 2, w["L"], w["N"])
-        for k, (l, t) in enumerate(slots):
+        out = self.out.view(w["B"], w["D1"], 2, w["L"], self.T)
+        for k, (l, t) in enumerate(local):
             want = oracle.rowsel(ct[:, :, :, None, k:k + 1], db[:, :, None, k:k + 1], [w["primes"][l]])[..., 0, 0]
             got = out[:, :, :, l, t].contiguous().cpu().numpy().view(np.uint32)
             if not np.array_equal(got, want):
@@ -756,7 +775,14 @@ def main():
     mask = 0
     for p in built:
         mask |= p
-    wl = GpuWorkload(g, torch, w, mask)
+    # N > 1: each rank keeps and computes its slot shard of the one workload
+    # (RowSel is independent per NTT point: no exchange while it runs)
+    sh = None
+    if world > 1:
+        from paper_2604_04696_gb300.shard import SlotShard
+        sh = SlotShard(w["N"], world, rank)
+    wl = GpuWorkload(g, torch, w, mask, shard=sh)
+    w_rank = dict(w, N=wl.T)      # this GPU's share, for its kernels' rooflines
 
     # choose the path: requested, else the fastest built path after autotuning each
     per_path = {}
@@ -779,29 +805,34 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    qps = world * w["B"] / (ms / 1e3)
+    qps = w["B"] / (ms / 1e3)      # the whole batch, all ranks together
     e2e_ms, h2d, d2h = wl.e2e(path, max(3, args.steps // 2), 2)
-    e2e_val = w["B"] / (e2e_ms / 1e3)
     if world > 1:
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * w["B"] / (float(t.item()) / 1e3)
+        e2e_ms = float(t.item())
+        h2d, d2h = h2d * world, d2h * world
+    e2e_val = w["B"] / (e2e_ms / 1e3)
 
     db_bytes = sizes.db_bytes(w["D0"], w["D1"], w["N"], w["L"])
     alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     line = {
         "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": {1: "u32 (u64 accumulate)", 2: "u8 (s32 accumulate)",
                                        4: "fp16 digits (fp32 exact accumulate)"}[path],
-        "data": "synthetic", "config": cfg_dict(args.workload, w, PATH_NAMES[path], variant),
+        "data": "synthetic",
+        "config": dict(cfg_dict(args.workload, w, PATH_NAMES[path], variant),
+                       parallelism=("slot shards: %d ranks x %d slots per limb, no collective in the step"
+                                    % (world, wl.T)) if world > 1 else "one GPU"),
         "db_gbs": db_bytes / (ms / 1e3) / 1e9, "alg_gbs": alg / (ms / 1e3) / 1e9,
         "bit_exact_sample": exact,
         # the dominant kernel's roofline: from the untraced step when the step is
         # that one launch, else from its traced per-launch time
-        "roofline": kernel_roofline(dom, w, ms if (len(kcount) == 1 and kcount[dom] == 1) else ktimes[dom],
+        "roofline": kernel_roofline(dom, w_rank, ms if (len(kcount) == 1 and kcount[dom] == 1) else ktimes[dom],
                                     peaks, args.workload),
-        "step_roofline": roofline(path, w, ms, peaks, args.workload),
+        "step_roofline": roofline(path, w_rank, ms, peaks, args.workload),
         "kernels": {k: {"ms": v, "launches_per_step": kcount[k], "share": v * kcount[k] / sum(
             ktimes[x] * kcount[x] for x in ktimes)} for k, v in ktimes.items()},
         "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

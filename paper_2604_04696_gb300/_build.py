@@ -17,8 +17,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgpir.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["gpir_abi.cu", "rowsel_cc.cu", "rowsel_imma.cu", "rowsel_tc.cu", "rowsel_multi.cu", "trace.cu", "coltor.cu", "expand.cu", "ring_tables.cu"]
-HEADERS = ["internal.h", "common.cuh", "ntt.cuh"]
+SOURCES = ["gpir_abi.cu", "rowsel_cc.cu", "rowsel_imma.cu", "rowsel_tc.cu", "rowsel_tmem.cu", "rowsel_multi.cu", "trace.cu", "coltor.cu", "expand.cu", "ring_tables.cu"]
+HEADERS = ["internal.h", "common.cuh", "ntt.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -367,6 +367,7 @@ int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1, const 
   if (rc != GPIR_OK) goto fail;
   if (path_mask & GPIR_PATH_TC) {
     rc = rowsel_tc_prepare(db, s);
+    if (rc == GPIR_OK) rc = rowsel_tmem_prepare(db, s);
     if (rc != GPIR_OK) goto fail;
   }
   *out = db;
@@ -380,6 +381,7 @@ int gpir_db_free(gpir_db_t *db) {
   if (!db) return GPIR_OK;
   if (db->db_pmajor) cudaFree(db->db_pmajor);
   if (db->db_digits) cudaFree(db->db_digits);
+  if (db->db_digits12) cudaFree(db->db_digits12);
   if (db->ws_ct) cudaFree(db->ws_ct);
   if (db->ws_out) cudaFree(db->ws_out);
   delete db->variants;
@@ -391,7 +393,7 @@ int gpir_db_free(gpir_db_t *db) {
 size_t gpir_db_device_bytes(const gpir_db_t *db) {
   if (!db) return 0;
   size_t b = (size_t)db->d0 * db->d1 * db->params.num_limbs * db->params.n * 4;
-  return b + db->db_digits_bytes;
+  return b + db->db_digits_bytes + db->db_digits12_bytes;
 }
 
 int gpir_rowsel_batch(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, uint32_t *out_dev, int path,

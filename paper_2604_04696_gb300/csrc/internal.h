@@ -48,9 +48,12 @@ struct gpir_db {
   int device;
   // CUDA-core and IMMA paths read the p-major database as uploaded.
   uint32_t *db_pmajor;          // [D0][D1][L][N]
-  // tcgen05 path: signed 8-bit digits as bf16, slot-major (see rowsel_tc.cu).
+  // tcgen05 path: balanced base-256 digits as fp16, slot-major (rowsel_tc.cu),
+  // and the three base-2^10 digits of the centred residues (rowsel_tmem.cu).
   uint16_t *db_digits;
   size_t db_digits_bytes;
+  uint16_t *db_digits12;
+  size_t db_digits12_bytes;
   // Host-buffer entry point workspace.
   uint32_t *ws_ct, *ws_out;
   size_t ws_ct_bytes, ws_out_bytes;
@@ -116,6 +119,15 @@ int trace_begin(const char *name, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
 bool trace_enabled();
 void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
+
+// Tensor-memory kernel (rowsel_tmem.cu): its database layout, built at upload,
+// and one launch (pair: the SM-pair form; GPIR_ENOTSUP if it does not apply).
+int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream);
+int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
+                   uint32_t lookahead_mb, bool pair, cudaStream_t stream);
+// The tensor-core workspace kept for (current device, stream), grown on demand
+// (never inside a stream capture: GPIR_ENOMEM then).
+int tc_stream_workspace(cudaStream_t stream, size_t need, uint8_t **out);
 
 int rowsel_tc_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
 // Free the tensor-core workspace kept for (current device, stream), if any.

@@ -54,6 +54,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace gpir {
 namespace {
@@ -119,164 +120,6 @@ __device__ __forceinline__ UnitRef decode_unit(const TcParams &p, uint64_t u) {
   r.nb = (uint32_t)(x % jb.nblk);
   r.slot = x / jb.nblk;
   return r;
-}
-
-// ---- PTX wrappers (tcgen05 / bulk copy) ------------------------------------
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
-                                              uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-      : "memory");
-}
-
-__device__ __forceinline__ void st_global_v4_hint(void *dst, const uint4 &v, uint64_t pol) {
-  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "r"(v.x),
-               "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
-               : "memory");
-}
-
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
-  return d;
-}
-
-// kind::f16, D = f32, A = B = f16 (format 0), both K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// Address of the same shared-memory offset in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t map_peer(uint32_t local_saddr, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_saddr), "r"(rank));
-  return r;
-}
-// Arrive on barrier `bar` (same offset) in every CTA of `mask` once the
-// MMAs issued so far have completed.
-__device__ __forceinline__ void mma_commit_cluster(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
-
-// ---- SM-pair (cta_group::2) wrappers -----------------------------------------
-//
-// kind::f16 across the two CTAs of a cluster pair: M = 256 (each CTA supplies
-// 128 rows of A from its own shared memory and receives them in its own
-// tensor memory), N = 256 (each CTA supplies half of the B rows, at the same
-// shared-memory offset), K = 16. Issued by one thread of the even CTA.
-constexpr uint32_t kIdescPair = (1u << 4) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
-      : "memory");
-}
-
-// Arrive on barrier `bar` (same offset) in both CTAs of the pair once the
-// pair MMAs issued so far have completed.
-__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"((uint16_t)3)
-      : "memory");
-}
-
-// Arrive (release, cluster scope) on a barrier of another CTA of the cluster,
-// given its shared::cluster address.
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-// Relaxed arrive on a barrier of another CTA of the cluster: a signal that
-// carries no data of this thread (a cluster-scope release would first wait
-// for this SM's outstanding global stores, microseconds under the ingest's
-// ring traffic).
-__device__ __forceinline__ void mbar_arrive_remote_relaxed(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-
-// try_wait with cluster-scope acquire: sees what a peer CTA wrote before its
-// release arrive on this barrier.
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void st_cluster_u64(uint32_t cluster_addr, uint64_t v) {
-  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(cluster_addr), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // ---- digit helpers -----------------------------------------------------------
@@ -763,20 +606,6 @@ enum FusedCounter {
   kCtaCycles,         // whole kernel, per CTA
   kNumFusedCounters
 };
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_cnt(uint64_t *bar, uint32_t cnt) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(cnt) : "memory");
-}
 
 template <bool PROF, bool PAIR>
 __global__ void __launch_bounds__(FUSED_THREADS, 1) tc_fused_kernel(const __grid_constant__ FusedParams p) {
@@ -2079,6 +1908,10 @@ int stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
 
 }  // namespace
 
+int tc_stream_workspace(cudaStream_t stream, size_t need, uint8_t **out) {
+  return stream_workspace(stream, need, out);
+}
+
 void rowsel_tc_release_stream(cudaStream_t stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
@@ -2096,7 +1929,14 @@ namespace {
 
 // Fused-kernel tile variants: digit-ring size (against the 129 MB L2) and L2
 // eviction hints; the autotuner picks one per shape.
-enum TcKernelKind : uint32_t { kKindFused = 0, kKindTwoPass = 1, kKindCluster = 2, kKindPair = 3 };
+enum TcKernelKind : uint32_t {
+  kKindFused = 0,
+  kKindTwoPass = 1,
+  kKindCluster = 2,
+  kKindPair = 3,
+  kKindTmem = 4,       // rowsel_tmem.cu: A in tensor memory, 12 digit products
+  kKindTmemPair = 5,   // its SM-pair form
+};
 struct FusedVariant {
   uint32_t kind;           // TcKernelKind
   uint32_t ring_mb;
@@ -2113,6 +1953,8 @@ constexpr FusedVariant kFusedVariants[] = {
     {kKindFused, 40, kHintRing, 16},    // 5
     {kKindCluster, 0, 0, 0},            // 6: 8-CTA clusters sharing raw boxes over DSMEM
     {kKindPair, 48, 0, 16},             // 7: SM pairs (cta_group::2) sharing each database tile
+    {kKindTmem, 48, 0, 16},             // 8: A operand in tensor memory, 12 digit products
+    {kKindTmemPair, 48, 0, 16},         // 9: its SM-pair form
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
@@ -2380,6 +2222,13 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
     job.ct = ct;
     job.out = out;
     return rowsel_tc_multi(&job, 1, stream);   // two-pass: ingest to HBM, then GEMM
+  }
+  if (v.kind == kKindTmem || v.kind == kKindTmemPair) {
+    const bool pr = v.kind == kKindTmemPair;
+    const int rc = tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, pr, stream);
+    if (rc != GPIR_ENOTSUP || !pr) return rc;
+    // an odd number of m-blocks (or no pair fits): the single-CTA form
+    return tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, false, stream);
   }
   if (v.kind == kKindPair) {
     const int rc = tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, true, stream);

@@ -1,0 +1,1069 @@
+// RowSel on the tensor cores with the A operand in tensor memory and 12 digit
+// products per modular MAC (the tensor-memory kernel, tile variants 8 and 9).
+//
+// What is computed: the per-point modular GEMM of Sec. 2.3 / Sec. 5.1 of the
+// GPIR paper, out[p][m][n] = sum_k ct[p][m][k] * db[p][k][n] mod q, with
+// p = (limb, slot), m = (client, polynomial), k = DB row, n = DB column.
+//
+// Exactness. Both operands are centred first (x -> x - q when x > (q-1)/2):
+// congruent mod q, magnitude below 2^27.
+//   - Ciphertext residues become four digits of 7 bits, d_u = field_u - 64 in
+//     [-64, 64], fields of y = x~ + O_A with O_A = 64 (1 + 2^7 + 2^14 + 2^21)
+//     (fields 0..2 are 7 bits, field 3 = y >> 21 <= 128).
+//   - Database residues become three digits, e_0, e_1 in [-512, 511] and
+//     e_2 in [-128, 128], of Y = v~ + O_B, O_B = 512 (1 + 2^10) (base 2^10,
+//     the top one by arithmetic shift).
+//   - A digit product has |d e| <= 2^15: a group of 512 rows sums to at most
+//     2^24 and every partial sum is an integer fp32 holds exactly. The tensor
+//     core computes the 12 group sums D_uv exactly, and
+//         out = sum_groups sum_{u,v} D_uv * (2^(7u + 10v) mod q)   (mod q)
+//     in 64-bit integers: < 2^55.6 per group, four groups (< 2^57.6) plus
+//     off58 (a multiple of q, >= 2^58) before one Barrett reduction.
+// Compared with the four-digit form of rowsel_tc.cu (16 products of base-256
+// digits), the tensor work and the database digit bytes drop by a quarter.
+//
+// Data movement. The database is packed once, at upload, into per-slot digit
+// tiles in the shared-memory image the MMA reads: [slot][n-block][k-chunk] x
+// (192 rows x 64 k) fp16, K-major, 128-byte swizzle, rows v*64 + n (24 KB).
+// Per batch, in one persistent launch (one CTA per SM, or per SM pair):
+//   - ingest warps TMA-load raw p-major boxes (8 slots x 32 rows x 64 k),
+//     encode every residue once into its 4 digit fields (one byte each) and
+//     store slot-major 8 KB tiles [32 rows][64 k] into a ring in global memory
+//     (4 bytes per residue, half the digit bytes), counted in ready[E % R];
+//   - the producer bulk-copies, per k-chunk of a unit, the ring tile (8 KB)
+//     and the database tile (24 KB, or its 12 KB half in the SM-pair form) into
+//     a shared-memory stage;
+//   - converter warps turn the ring tile into fp16 digits in registers (one
+//     PRMT, LOP3 and HADD2 per pair of digits) and store them straight into a
+//     tensor-memory A buffer (tcgen05.st): no digit tile in shared memory, and
+//     the MMA reads only B from shared memory;
+//   - one thread issues tcgen05.mma .kind::f16 with A in tensor memory
+//     (M = 128 or 256, N = 192, K = 16);
+//   - epilogue warps drain the double-buffered accumulators and a store warp
+//     writes the p-major output.
+// Tensor memory (512 columns): accumulators at [0, 192) and [192, 384), four
+// A buffers of 32 columns (64 k of fp16 pairs) at 384 + 32 st.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+namespace gpir {
+namespace {
+
+constexpr int T_KCHUNK = 64;                         // k per stage
+constexpr int T_MROWS = 32;                          // ciphertext rows per tile (x 4 digits = 128 lanes)
+constexpr int T_NCOLS = 64;                          // DB columns per tile (x 3 digits = 192)
+constexpr int T_NDIG = 3 * T_NCOLS;                  // MMA N
+constexpr int T_KGROUP = 8;                          // k-chunks per exact group: 512 rows
+constexpr int T_FLUSH = 4;                           // groups summed before one reduction
+constexpr int T_RAW_TILE = T_MROWS * T_KCHUNK * 4;   // 8 KB ring tile
+constexpr int T_B_TILE = T_NDIG * T_KCHUNK * 2;      // 24 KB
+constexpr int T_STAGES = 4;
+constexpr uint32_t T_ACC_COLS = T_NDIG;
+constexpr uint32_t T_A_COL0 = 2 * T_ACC_COLS;        // 384
+constexpr uint32_t T_TMEM_COLS = 512;
+constexpr uint32_t kOffA = 64u * (1u + (1u << 7) + (1u << 14) + (1u << 21));
+constexpr int32_t kOffB = 512 * (1 + (1 << 10));
+
+// Warp roles (640 threads).
+constexpr int W_PROD = 0, W_MMA = 1, W_STORE = 2;
+constexpr int W_CONV0 = 4;                           // 4 converter warps: lane quarters 0..3
+constexpr int W_EPI0 = 8, N_EPI = 8;                 // 8 epilogue warps: quarter = warp & 3, column half
+constexpr int W_ING0 = 16, N_ING = 4;                // 4 ingest warps
+constexpr int T_THREADS = 32 * (W_ING0 + N_ING);     // 640
+constexpr int T_RAW_BOX = 16 * T_KCHUNK * 2 * 8 * 4; // 64 KB: 16 clients x 64 k x 2 x 8 slots
+constexpr int T_OUT_BYTES = T_MROWS * T_NCOLS * 4;   // 8 KB
+
+template <bool PAIR>
+struct TmemCfg {
+  static constexpr int B_BYTES = PAIR ? T_B_TILE / 2 : T_B_TILE;   // this CTA's part of B
+  static constexpr int STAGE = T_RAW_TILE + B_BYTES;
+  static constexpr size_t SMEM = 1024 + (size_t)T_STAGES * STAGE + T_RAW_BOX + T_OUT_BYTES + 512;
+};
+static_assert(TmemCfg<false>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
+static_assert(TmemCfg<true>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
+
+struct TmLimb {
+  uint32_t q, h;         // prime, (q - 1) / 2
+  uint64_t mu;           // floor(2^64 / q)
+  uint64_t off58;        // multiple of q, >= 2^58
+  int32_t w[4][3];       // 2^(7u + 10v) mod q
+};
+
+struct TmemParams {
+  uint32_t L, N, M, d0, d1, mblk, nblk, kch;
+  uint32_t R, gpl, spg, lookahead;
+  uint64_t n_entries, upe, n_units, n_tasks;
+  const uint16_t *b_tiles;              // [slot][nblk][kch] x 24 KB
+  uint32_t *out;
+  uint8_t *ring;                        // [R][8 slots][kch] x 8 KB
+  uint32_t *ready, *consumed;           // [R] each
+  unsigned long long *ctr;              // [0] next unit, [1] next ingest task
+  unsigned int *err;
+  unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
+  TmLimb limb[GPIR_MAX_LIMBS];
+};
+
+// Wait / busy cycle counters of the traced instantiation (SM clock cycles
+// summed over CTAs, one counting thread per role), read through
+// gpir_trace_counters.
+enum TmemCounter {
+  kTPWaitReady = 0,   // producer: ring entry not yet ingested
+  kTPWaitEmpty,       // producer: no free stage
+  kTCWaitFull,        // converter: stage not landed
+  kTCBusy,            // converter: converting and storing to tensor memory
+  kTMWaitA,           // MMA: A buffer not converted
+  kTMWaitAcc,         // MMA: accumulator not drained
+  kTEWaitAcc,         // epilogue: MMAs of the group not done
+  kTEBusy,            // epilogue: draining and reducing
+  kTIWaitSlot,        // ingest: ring entry not released, or lookahead
+  kTIWaitBox,         // ingest: TMA box in flight
+  kTIBusy,            // ingest: encoding and ring stores
+  kTIFence,           // ingest: fence and ready count
+  kTCta,              // kernel cycles per CTA
+  kNumTmemCounters
+};
+
+constexpr uint64_t kNoUnit = ~0ull;
+
+// kind::f16, D = f32, A = B = f16, K-major, N = 192, M = 128 (one CTA) or 256 (pair).
+constexpr uint32_t kIdescT1 = (1u << 4) | ((uint32_t)(T_NDIG >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescT2 = (1u << 4) | ((uint32_t)(T_NDIG >> 3) << 17) | ((256u >> 4) << 24);
+
+// D[tmem_d] (+)= A[tmem_a] * B[bdesc]: A read from tensor memory (lane = row,
+// column j = k pair 2j, 2j+1), B from shared memory.
+__device__ __forceinline__ void mma_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(kIdescT1), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tmem_a_pair(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                                uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(kIdescT2), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive tensor-memory columns of this warp's lane quarter <- r[0..31].
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+// Three loads of 8 columns each (the three database digits of 8 columns).
+__device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t (&r)[24]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(t0), "r"(t1), "r"(t2));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Ring encoding of a ciphertext residue x < q: the four 7-bit fields of
+// y = centred(x) + O_A, one per byte (bit 7 of bytes 0..2 is don't-care,
+// byte 3 holds y >> 21 <= 128 whole).
+__device__ __forceinline__ uint32_t ct_fields(uint32_t x, uint32_t q, uint32_t h) {
+  const uint32_t y = x + kOffA - (x > h ? q : 0u);
+  uint32_t z = (y & 0x7Fu) | ((y << 1) & 0xFFFFFF80u);
+  z = (z & 0x7FFFu) | ((y << 2) & 0xFFFF8000u);
+  z = (z & 0x7FFFFFu) | ((y << 3) & 0xFF800000u);
+  return z;
+}
+
+// fp16 pair (digit u of z0, digit u of z1): byte u of each under 0x6400
+// (= 1024 + field exactly), then field - 64 by one HADD2.
+// sel = u | u << 4 | (u + 4) << 8 | (u + 4) << 12 picks byte u of z0 and of z1;
+// mask keeps 7 bits (8 for the top digit u = 3). Both are per-thread values,
+// so a warp whose lanes hold different digits runs one instruction stream.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t z0, uint32_t z1, uint32_t sel, uint32_t mask) {
+  const uint32_t t = (__byte_perm(z0, z1, sel) & mask) | 0x64006400u;
+  const __half2 h = __hadd2(*reinterpret_cast<const __half2 *>(&t),
+                            __half2half2(__ushort_as_half((unsigned short)0xE440)));   // -1088
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// fp16 bit pattern of database digit v (0..2) of a residue below q.
+__device__ __forceinline__ uint16_t db_digit_bits(uint32_t x, uint32_t q, int v) {
+  const int32_t xt = (int32_t)x - (x > (q - 1) / 2 ? (int32_t)q : 0);
+  const int32_t Y = xt + kOffB;
+  const int32_t e = v == 0 ? (Y & 1023) - 512 : v == 1 ? ((Y >> 10) & 1023) - 512 : (Y >> 20);
+  return __half_as_ushort(__int2half_rn(e));   // |e| <= 512: exact
+}
+
+// ---- database packing (once per upload) -------------------------------------
+
+struct Pack12Params {
+  uint32_t d0, d1, L, N, nblk, kch;
+  const uint32_t *db;
+  uint4 *b_tiles;
+  uint32_t q[GPIR_MAX_LIMBS];
+};
+
+// One thread per (slot, n-block, k-chunk, digit row, k octet); slots fastest so
+// the reads of the p-major database are coalesced. Row r = v * 64 + n of the
+// 192-row tile, 16-byte chunk (k octet) j stored at j ^ (r % 8): the 128-byte
+// swizzle of the MMA's shared-memory operand.
+__global__ void tm_pack_db_kernel(const Pack12Params p, uint64_t total) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = i;
+    const uint32_t slot = (uint32_t)(x % ((uint64_t)p.L * p.N));
+    x /= (uint64_t)p.L * p.N;
+    const uint32_t k_oct = (uint32_t)(x % 8);
+    x /= 8;
+    const uint32_t row = (uint32_t)(x % T_NDIG);
+    x /= T_NDIG;
+    const uint32_t kc = (uint32_t)(x % p.kch);
+    const uint32_t nb = (uint32_t)(x / p.kch);
+    const uint32_t v = row / T_NCOLS, n = nb * T_NCOLS + row % T_NCOLS;
+    const uint32_t l = slot / p.N, t = slot % p.N;
+    uint32_t bits[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint32_t k = kc * T_KCHUNK + k_oct * 8 + kk;
+      bits[kk] = (n < p.d1 && k < p.d0)
+                     ? db_digit_bits(p.db[(((uint64_t)k * p.d1 + n) * p.L + l) * p.N + t], p.q[l], (int)v)
+                     : 0u;   // padding: digit 0
+    }
+    uint4 w;
+    w.x = bits[0] | (bits[1] << 16);
+    w.y = bits[2] | (bits[3] << 16);
+    w.z = bits[4] | (bits[5] << 16);
+    w.w = bits[6] | (bits[7] << 16);
+    p.b_tiles[(((uint64_t)slot * p.nblk + nb) * p.kch + kc) * (T_B_TILE / 16) + row * 8 + (k_oct ^ (row & 7))] = w;
+  }
+}
+
+// ---- the persistent kernel -------------------------------------------------
+//
+// Work: entries E = (8-slot group g, 32-row m-block), units (E, slot, n-block)
+// of kch k-chunks, ingest tasks (E, k-chunk). Claiming, ring flow control and
+// the deadlock argument are those of the fused kernel in rowsel_tc.cu (both
+// sides claim in increasing order; an ingest task waits only for the ring
+// entry R back and for claims already made); here the ring holds encoded raw
+// residues and the entry is released as soon as its unit's last k-chunk has
+// landed in shared memory. SM-pair form (PAIR): a pair unit covers entries
+// 2 E2 (even CTA) and 2 E2 + 1 (odd CTA) against one database tile; each CTA
+// copies its own ring tile and its half of B and converts its own A into its
+// own tensor memory; the even CTA's MMA thread issues M = 256 MMAs once both
+// CTAs' A buffers are ready; commits go to both CTAs.
+template <bool PROF, bool PAIR>
+__global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_constant__ TmemParams p) {
+  using Cfg = TmemCfg<PAIR>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // stage st: B part at smem + st * STAGE (1024-aligned), ring tile after it
+  uint8_t *rawbox = smem + T_STAGES * Cfg::STAGE;
+  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + T_RAW_BOX);
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + T_RAW_BOX + T_OUT_BYTES);
+  uint64_t *empty = full + T_STAGES;
+  uint64_t *afull = empty + T_STAGES;             // A buffer st converted (and, pair: both CTAs')
+  uint64_t *acc_full = afull + T_STAGES;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *box_bar = acc_empty + 2;
+  uint64_t *ostage_full = box_bar + 1;
+  uint64_t *ostage_empty = ostage_full + 1;
+  uint64_t *stage_unit = ostage_empty + 1;        // [T_STAGES]
+  uint64_t *acc_unit = stage_unit + T_STAGES;     // [2]
+  uint64_t *task_slot = acc_unit + 2;
+  uint64_t *ostage_unit = task_slot + 1;
+  uint64_t *mail = ostage_unit + 1;               // pair: [4] claimed units, even -> odd CTA
+  uint64_t *mail_full = mail + 4;
+  uint64_t *mail_empty = mail_full + 4;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail_empty + 4);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      // single CTA: the 4 converter warps; pair (even CTA): both CTAs' converter warps
+      mbar_init(&afull[s], (PAIR && rank == 0) ? 8 : 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 2);
+      mbar_init(&acc_empty[b], (PAIR && rank == 0) ? 2 * N_EPI : N_EPI);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&mail_full[i], 1);
+      mbar_init(&mail_empty[i], 1);
+    }
+    mbar_init(box_bar, 1);
+    mbar_init(ostage_full, N_EPI);
+    mbar_init(ostage_empty, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == W_MMA) {
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(T_TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(T_TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+  }
+  tc_fence_before();
+  if constexpr (PAIR)
+    cluster_sync_all();
+  else
+    __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto try_wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    if constexpr (PAIR)
+      return mbar_try_wait_cluster(bar, parity);
+    else
+      return mbar_try_wait(bar, parity);
+  };
+  auto wait = [&](uint64_t *bar, uint32_t parity, unsigned int code) -> bool {
+    if (try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      if (try_wait(bar, parity)) return true;
+      if ((n & 63u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, code);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  auto wait_claims = [&](uint64_t target) -> bool {
+    auto seen = [&]() {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&p.ctr[0]) : "memory");
+      return v >= target;
+    };
+    if (seen()) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      __nanosleep(64);
+      if (seen()) return true;
+      if ((n & 15u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, (unsigned int)kErrQueueWait);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  auto wait_count = [&](const uint32_t *ctr, uint32_t target) -> bool {
+    if (ld_acquire(ctr) >= target) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t n = 1;; ++n) {
+      __nanosleep(64);
+      if (ld_acquire(ctr) >= target) return true;
+      if ((n & 15u) == 0) {
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(p.err, 0u, (unsigned int)kErrQueueWait);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
+  // entry of a unit for this CTA
+  auto entry_of = [&](uint64_t u) -> uint64_t { return PAIR ? (u / p.upe) * 2 + rank : u / p.upe; };
+  uint64_t pc[PROF ? kNumTmemCounters : 1];
+#pragma unroll
+  for (int i = 0; i < (PROF ? kNumTmemCounters : 1); ++i) pc[i] = 0;
+  const uint64_t kstart = PROF ? clock64() : 0;
+#define TM_TIMED(k, expr)                                 \
+  ([&]() {                                                 \
+    const uint64_t _t0 = PROF ? clock64() : 0;             \
+    const bool _r = (expr);                                \
+    if (PROF) pc[PROF ? (k) : 0] += clock64() - _t0;       \
+    return _r;                                             \
+  }())
+
+  if (warp == W_PROD) {
+    // ---------------- producer: claims units, copies ring + B tiles ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, mi = 0;
+      bool ok = true;
+      for (;;) {
+        uint64_t u;
+        if constexpr (PAIR) {
+          const uint32_t ms = mi & 3u, mph = (mi >> 2) & 1u;
+          ++mi;
+          if (rank == 0) {
+            u = atomicAdd(&p.ctr[0], 1ull);
+            if (u >= p.n_units) u = kNoUnit;
+            if (!(ok = wait(&mail_empty[ms], mph ^ 1u, kErrQueueWait))) break;
+            st_cluster_u64(map_peer(smem_u32(&mail[ms]), 1), u);
+            mbar_arrive_remote(map_peer(smem_u32(&mail_full[ms]), 1));
+          } else {
+            if (!(ok = wait(&mail_full[ms], mph, kErrQueueWait))) break;
+            u = *reinterpret_cast<volatile uint64_t *>(&mail[ms]);
+            mbar_arrive_remote(map_peer(smem_u32(&mail_empty[ms]), 0));
+          }
+          if (u == kNoUnit) break;
+        } else {
+          u = atomicAdd(&p.ctr[0], 1ull);
+          if (u >= p.n_units) break;
+        }
+        const uint64_t E = entry_of(u);
+        const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+        const uint32_t g = (uint32_t)(E / p.mblk);
+        const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
+        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
+        fence_proxy_async_global();
+        const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
+        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
+                               (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
+        for (uint32_t kc = 0; kc < p.kch; ++kc) {
+          if (!(ok = TM_TIMED(kTPWaitEmpty, wait(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
+          stage_unit[st] = u;
+          uint8_t *sb = smem + st * Cfg::STAGE;
+          mbar_arrive_expect_tx(&full[st], Cfg::STAGE);
+          bulk_g2s(sb, b_src + (uint64_t)kc * T_B_TILE, Cfg::B_BYTES, &full[st]);
+          bulk_g2s(sb + Cfg::B_BYTES, a_src + (uint64_t)kc * T_RAW_TILE, T_RAW_TILE, &full[st]);
+          if (++st == T_STAGES) {
+            st = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      if (ok && wait(&empty[st], ph ^ 1u, kErrTmaWait)) {
+        stage_unit[st] = kNoUnit;   // end of work
+        mbar_arrive(&full[st]);
+        if constexpr (PAIR) {
+          // the last multicast commits target this CTA's empty barriers too:
+          // let them land (every stage but the sentinel's) before the CTA leaves
+          for (int s2 = 1; s2 < T_STAGES; ++s2) {
+            if (++st == T_STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+            mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
+          }
+        }
+      } else {
+        for (int s2 = 0; s2 < T_STAGES; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
+      }
+    }
+  } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
+    // ---------------- converters: ring tile (smem) -> fp16 digits -> tensor memory ----------------
+    // Thread = tensor-memory lane (row m_hi*32 + u*8 + m_lo of the A operand):
+    // ciphertext row m = m_hi*8 + m_lo of the m-block, digit u.
+    const uint32_t qw = (uint32_t)(warp & 3);
+    const int u = lane >> 3, m_lo = lane & 7;
+    const int m = (int)qw * 8 + m_lo;
+    const uint32_t lane_base = tmem_base + ((qw * 32u) << 16);
+    const uint32_t dsel = (uint32_t)(u | (u << 4) | ((u + 4) << 8) | ((u + 4) << 12));
+    const uint32_t dmask = u < 3 ? 0x007F007Fu : 0x00FF00FFu;
+    uint32_t st = 0, ph = 0;
+    uint32_t kc_seen = 0;                 // k-chunks of the current unit seen so far
+    const bool conv_counter = PROF && qw == 0 && lane == 0;
+    for (;;) {
+      const bool okf = conv_counter ? TM_TIMED(kTCWaitFull, wait(&full[st], ph, kErrTmaWait))
+                                    : wait(&full[st], ph, kErrTmaWait);
+      if (!__all_sync(0xffffffffu, okf)) break;
+      const uint64_t tconv = PROF ? clock64() : 0;
+      const uint64_t un = stage_unit[st];
+      if (un == kNoUnit) {
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR && rank != 0)
+            mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[st]), 0));
+          else
+            mbar_arrive(&afull[st]);
+        }
+        break;
+      }
+      if (++kc_seen == p.kch) {
+        kc_seen = 0;
+        // the unit's last ring tile is in shared memory: its ring entry may be reused
+        if (qw == 0 && lane == 0) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
+      }
+      const uint4 *row = reinterpret_cast<const uint4 *>(smem + st * Cfg::STAGE + Cfg::B_BYTES) + m * 16;
+      uint32_t wv[32];
+#pragma unroll
+      for (int c16 = 0; c16 < 16; ++c16) {
+        const uint4 z = row[c16 ^ (m & 7)];
+        wv[2 * c16] = digit_pair(z.x, z.y, dsel, dmask);
+        wv[2 * c16 + 1] = digit_pair(z.z, z.w, dsel, dmask);
+      }
+      tmem_st32(lane_base + T_A_COL0 + st * 32u, wv);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR && rank != 0)
+          mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[st]), 0));
+        else
+          mbar_arrive(&afull[st]);
+      }
+      if (conv_counter) pc[PROF ? kTCBusy : 0] += clock64() - tconv;
+      if (++st == T_STAGES) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+  } else if (warp == W_MMA) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, buf = 0;
+      uint32_t aph[2] = {0, 0};
+      bool ok = true;
+      const uint32_t kgroups = (p.kch + T_KGROUP - 1) / T_KGROUP;
+      for (;;) {
+        if (PAIR && rank != 0) {
+          // odd CTA: its converters signal the even CTA directly; nothing to issue
+          break;
+        }
+        if (!(ok = TM_TIMED(kTMWaitA, wait(&afull[st], ph, kErrTmaWait)))) break;
+        const uint64_t u = stage_unit[st];
+        if (u == kNoUnit) {
+          if ((ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
+            acc_unit[buf] = kNoUnit;
+            if constexpr (PAIR) {
+              // the odd CTA's epilogue learns the end of work from its own acc_unit
+              st_cluster_u64(map_peer(smem_u32(&acc_unit[buf]), 1), kNoUnit);
+              mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
+              mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
+            }
+            mbar_arrive_cnt(&acc_full[buf], 2);
+          }
+          break;
+        }
+        bool first = true;
+        for (uint32_t gi = 0; gi < kgroups && ok; ++gi) {
+          if (!(ok = TM_TIMED(kTMWaitAcc, wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait)))) break;
+          tc_fence_after();
+          const uint32_t tmem_d = tmem_base + buf * T_ACC_COLS;
+          const uint32_t c0 = gi * T_KGROUP;
+          const uint32_t c1 = min(p.kch, c0 + T_KGROUP);
+          for (uint32_t kc = c0; kc < c1; ++kc) {
+            if (!first && !(ok = TM_TIMED(kTMWaitA, wait(&afull[st], ph, kErrTmaWait)))) break;
+            first = false;
+            tc_fence_after();
+            const uint32_t sb = smem_u32(smem + st * Cfg::STAGE);
+            const uint32_t ta = tmem_base + T_A_COL0 + st * 32u;
+#pragma unroll
+            for (int k16 = 0; k16 < T_KCHUNK / 16; ++k16) {
+              const uint32_t acc = (kc > c0 || k16 > 0) ? 1u : 0u;
+              if constexpr (PAIR)
+                mma_tmem_a_pair(tmem_d, ta + k16 * 8, sw128_desc(sb + k16 * 32), acc);
+              else
+                mma_tmem_a(tmem_d, ta + k16 * 8, sw128_desc(sb + k16 * 32), acc);
+            }
+            if constexpr (PAIR)
+              mma_commit_pair(&empty[st]);
+            else
+              mma_commit(&empty[st]);
+            if (++st == T_STAGES) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          const uint64_t tag = u | ((gi + 1 == kgroups) ? (1ull << 63) : 0ull);
+          acc_unit[buf] = tag;
+          if constexpr (PAIR) {
+            st_cluster_u64(map_peer(smem_u32(&acc_unit[buf]), 1), tag);
+            mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
+            mma_commit_pair(&acc_full[buf]);
+          } else {
+            mma_commit(&acc_full[buf]);
+          }
+          mbar_arrive(&acc_full[buf]);
+          aph[buf] ^= 1u;
+          buf ^= 1u;
+        }
+        if (!ok) break;
+      }
+      if (!ok && !(PAIR && rank != 0))
+        for (int b = 0; b < 2; ++b) mbar_wait_bounded(&acc_full[b], aph[b], nullptr, 0);
+    }
+  } else if (warp >= W_EPI0 && warp < W_EPI0 + N_EPI) {
+    // ---------------- epilogue (8 warps) ----------------
+    const uint32_t qw = (uint32_t)(warp & 3);
+    const uint32_t half = (uint32_t)(warp - W_EPI0) >> 2;   // columns [32 half, 32 half + 32)
+    const int u = lane >> 3, m_lo = lane & 7;
+    const int m_local = (int)qw * 8 + m_lo;
+    const int et = (int)threadIdx.x - 32 * W_EPI0;
+    auto epi_all = [&](bool v) -> bool {
+      uint32_t r = v ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 2, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(r)
+          : "r"(r), "n"(32 * N_EPI)
+          : "memory");
+      return r != 0;
+    };
+    uint32_t buf = 0, oph = 0, ngroups = 0;
+    uint32_t aph[2] = {0, 0};
+    uint32_t res[8];
+    int64_t acc64[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      res[i] = 0;
+      acc64[i] = 0;
+    }
+    const bool epi_counter = PROF && et == 0;
+    for (;;) {
+      const bool oka = epi_counter ? TM_TIMED(kTEWaitAcc, wait(&acc_full[buf], aph[buf], kErrMmaWait))
+                                   : wait(&acc_full[buf], aph[buf], kErrMmaWait);
+      if (!epi_all(oka)) break;
+      const uint64_t tepi = PROF ? clock64() : 0;
+      tc_fence_after();
+      const uint64_t tag = acc_unit[buf];
+      if (tag == kNoUnit) {
+        if (epi_all(wait(ostage_empty, oph ^ 1u, kErrMmaWait))) {
+          if (et == 0) *ostage_unit = kNoUnit;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(ostage_full);
+        }
+        break;
+      }
+      const uint64_t un = tag & ~(1ull << 63);
+      const bool last = (tag >> 63) != 0;
+      const uint64_t E = entry_of(un);
+      const uint32_t l = (uint32_t)(E / p.mblk) / p.gpl;
+      const TmLimb &lm = p.limb[l];
+      const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
+      const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t d[24];
+        tmem_ld8x3(tbase + c * 8, tbase + 64 + c * 8, tbase + 128 + c * 8, d);
+        int64_t P[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          P[i] = (int64_t)__float2int_rn(__uint_as_float(d[i])) * w0 +
+                 (int64_t)__float2int_rn(__uint_as_float(d[8 + i])) * w1 +
+                 (int64_t)__float2int_rn(__uint_as_float(d[16 + i])) * w2;
+        // reduce-scatter over the 4 digits u (lanes u*8 + m_lo): thread u keeps
+        // columns c*8 + u and c*8 + 4 + u
+        const int b0 = u & 1, b1 = (u >> 1) & 1;
+        int64_t K1[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int64_t keep = b0 ? P[2 * i + 1] : P[2 * i];
+          const int64_t send = b0 ? P[2 * i] : P[2 * i + 1];
+          K1[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int64_t keep = b1 ? K1[2 * i + 1] : K1[2 * i];
+          const int64_t send = b1 ? K1[2 * i] : K1[2 * i + 1];
+          acc64[c * 2 + i] += keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&acc_empty[buf]);
+        if (PAIR && rank != 0) mbar_arrive_remote_relaxed(map_peer(smem_u32(&acc_empty[buf]), 0));
+      }
+      aph[buf] ^= 1u;
+      buf ^= 1u;
+      if (epi_counter) pc[PROF ? kTEBusy : 0] += clock64() - tepi;
+      if (last || ++ngroups == T_FLUSH) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t rr = reduce64((uint64_t)(acc64[i] + (int64_t)lm.off58), lm.q, lm.mu);
+          const uint32_t a = res[i] + rr;
+          res[i] = a >= lm.q ? a - lm.q : a;
+          acc64[i] = 0;
+        }
+        ngroups = 0;
+      }
+      if (last) {
+        if (!epi_all(wait(ostage_empty, oph ^ 1u, kErrMmaWait))) break;
+        const uint32_t swz = (uint32_t)m_lo << 2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const uint32_t n = half * 32u + c * 8u + i * 4u + (uint32_t)u;
+            out_stage[m_local * T_NCOLS + (n ^ swz)] = res[c * 2 + i];
+          }
+        if (et == 0) *ostage_unit = un;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ostage_full);
+        oph ^= 1u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) res[i] = 0;
+      }
+    }
+  } else if (warp == W_STORE) {
+    // ---------------- output store warp ----------------
+    uint32_t ph = 0;
+    for (;;) {
+      if (!__all_sync(0xffffffffu, wait(ostage_full, ph, kErrMmaWait))) break;
+      const uint64_t un = *ostage_unit;
+      if (un == kNoUnit) break;
+      const uint64_t E = entry_of(un);
+      const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
+      const uint32_t mrows = min((uint32_t)T_MROWS, p.M - mb * T_MROWS);
+      const uint32_t ncols = min((uint32_t)T_NCOLS, p.d1 - nb * T_NCOLS);
+      const uint64_t nstride = (uint64_t)2 * p.L * p.N;
+      for (uint32_t mm = 0; mm < mrows; ++mm) {
+        const uint32_t mg = mb * T_MROWS + mm, c = mg >> 1, rr = mg & 1;
+        const uint32_t sw = (mm & 7u) << 2;
+        uint32_t *orow = p.out + (((uint64_t)c * p.d1 + nb * T_NCOLS) * 2 + rr) * p.L * p.N + (uint64_t)l * p.N + t;
+#pragma unroll
+        for (uint32_t hh = 0; hh < T_NCOLS / 32; ++hh) {
+          const uint32_t n = hh * 32 + lane;
+          if (n < ncols) orow[n * nstride] = out_stage[mm * T_NCOLS + (n ^ sw)];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ostage_empty);
+      ph ^= 1u;
+    }
+  } else if (warp >= W_ING0) {
+    // ---------------- ingest (4 warps, 128 threads) ----------------
+    // Task = (entry E, k-chunk kc): one 64 KB TMA box of 8 slots x 32 rows x
+    // 64 k. Thread it handles items it and it + 128 of the 256 (row, k octet)
+    // items; for each slot it stores the 8 encoded residues of its row and
+    // octet as two 16-byte chunks of the slot's ring tile, chunk c16 of row m
+    // at position c16 ^ (m % 8) (conflict-free reads by the converters).
+    const int it = (warp - W_ING0) * 32 + lane;
+    constexpr int NT = 32 * N_ING;
+    uint32_t rph = 0;
+    bool issued = false;
+    for (;;) {
+      if (it == 0) {
+        const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
+        *task_slot = (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      const uint64_t c = *task_slot;
+      if (c == kNoUnit) break;
+      const uint64_t E = c / p.kch;
+      const uint32_t kc = (uint32_t)(c % p.kch);
+      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      if (it == 0) {
+        const bool near = p.lookahead == 0 || E < p.lookahead ||
+                          TM_TIMED(kTIWaitSlot, wait_claims(((E - p.lookahead) >> (PAIR ? 1 : 0)) * p.upe));
+        if (near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
+                                                                   (uint32_t)((E / p.R) * p.upe))))) {
+          mbar_arrive_expect_tx(box_bar, T_RAW_BOX);
+          tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
+                      (int)(mb * (T_MROWS / 2)));
+          issued = true;
+          *task_slot = c;
+        } else {
+          *task_slot = kNoUnit;
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      if (*task_slot == kNoUnit) break;
+      uint32_t got = (it == 0 ? TM_TIMED(kTIWaitBox, wait(box_bar, rph, kErrTmaWait))
+                              : wait(box_bar, rph, kErrTmaWait)) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
+          " selp.u32 %0, 1, 0, pout;\n}"
+          : "=r"(got)
+          : "r"(got), "n"(NT)
+          : "memory");
+      if (!got) break;
+      rph ^= 1u;
+      if (it == 0) issued = false;
+      const uint64_t tbusy = PROF ? clock64() : 0;
+      const uint32_t q = p.limb[l].q, h = p.limb[l].h;
+      const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox);
+      uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
+#pragma unroll 1
+      for (int item = it; item < 256; item += NT) {
+        const int m_local = item >> 3, j = item & 7;
+        const int cc = m_local >> 1, rp = m_local & 1;
+#pragma unroll
+        for (int s4 = 0; s4 < 2; ++s4) {
+          uint32_t z[8][4];   // [kk][slot in half]
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint4 v = raw4[((cc * T_KCHUNK + j * 8 + kk) * 2 + rp) * 2 + s4];
+            z[kk][0] = ct_fields(v.x, q, h);
+            z[kk][1] = ct_fields(v.y, q, h);
+            z[kk][2] = ct_fields(v.z, q, h);
+            z[kk][3] = ct_fields(v.w, q, h);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int sl = s4 * 4 + i;
+            if (t0 + sl >= p.N) continue;
+            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
+            uint4 lo, hi;
+            lo.x = z[0][i];
+            lo.y = z[1][i];
+            lo.z = z[2][i];
+            lo.w = z[3][i];
+            hi.x = z[4][i];
+            hi.y = z[5][i];
+            hi.z = z[6][i];
+            hi.w = z[7][i];
+            tile[m_local * 16 + ((2 * j) ^ (m_local & 7))] = lo;
+            tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))] = hi;
+          }
+        }
+      }
+      fence_proxy_async_global();
+      const uint64_t tfence = PROF ? clock64() : 0;
+      if (PROF && it == 0) pc[PROF ? kTIBusy : 0] += tfence - tbusy;
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      if (it == 0) {
+        __threadfence();
+        atomicAdd(&p.ready[E % p.R], 1u);
+        if (PROF) pc[PROF ? kTIFence : 0] += clock64() - tfence;
+      }
+    }
+    if (it == 0 && issued) mbar_wait_bounded(box_bar, rph, nullptr, 0);
+  }
+#undef TM_TIMED
+  if (PROF) {
+    // one counting thread per role: producer, MMA, converter warp 0, epilogue thread 0, ingest thread 0
+    const bool counter = lane == 0 && (warp == W_PROD || warp == W_MMA || warp == W_CONV0 || warp == W_EPI0 ||
+                                       warp == W_ING0);
+    if (counter)
+      for (int i = 0; i < (PROF ? kNumTmemCounters : 1) - 1; ++i)
+        if (pc[i]) atomicAdd(&p.prof[i], pc[i]);
+    if (threadIdx.x == 0) atomicAdd(&p.prof[kTCta], clock64() - kstart);
+  }
+  tc_fence_before();
+  if constexpr (PAIR)
+    cluster_sync_all();
+  else
+    __syncthreads();
+  tc_fence_after();
+  if (warp == W_MMA) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(T_TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(T_TMEM_COLS)
+                   : "memory");
+  }
+}
+
+TmLimb make_tm_limb(uint32_t q) {
+  TmLimb t;
+  t.q = q;
+  t.h = (q - 1) / 2;
+  t.mu = ~0ull / q;
+  const uint64_t two58 = 1ull << 58;
+  t.off58 = ((two58 + q - 1) / q) * (uint64_t)q;
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 3; ++v) {
+      uint64_t pw = 1;
+      for (int e = 0; e < 7 * u + 10 * v; ++e) pw = (pw * 2) % q;
+      t.w[u][v] = (int32_t)pw;
+    }
+  return t;
+}
+
+std::mutex g_tm_mu;
+bool g_tm_attr_done[64];
+int g_tm_pairs[64];   // resident CTA pairs of the pair form per device (-1: none)
+
+cudaLaunchConfig_t tm_pair_config(unsigned grid, cudaStream_t stream, cudaLaunchAttribute *attr) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(T_THREADS);
+  cfg.dynamicSmemBytes = TmemCfg<true>::SMEM;
+  cfg.stream = stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+}  // namespace
+
+int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream) {
+  const uint32_t L = db->params.num_limbs, N = db->params.n;
+  const uint32_t nblk = (db->d1 + T_NCOLS - 1) / T_NCOLS, kch = (db->d0 + T_KCHUNK - 1) / T_KCHUNK;
+  const uint64_t slots = (uint64_t)L * N;
+  const size_t bytes = (size_t)slots * nblk * kch * T_B_TILE;
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&db->db_digits12), bytes);
+  if (e != cudaSuccess) {
+    db->db_digits12 = nullptr;
+    return set_cuda_error(e);
+  }
+  db->db_digits12_bytes = bytes;
+  Pack12Params pp;
+  memset(&pp, 0, sizeof(pp));
+  pp.d0 = db->d0;
+  pp.d1 = db->d1;
+  pp.L = L;
+  pp.N = N;
+  pp.nblk = nblk;
+  pp.kch = kch;
+  pp.db = db->db_pmajor;
+  pp.b_tiles = reinterpret_cast<uint4 *>(db->db_digits12);
+  for (uint32_t l = 0; l < L; ++l) pp.q[l] = db->params.primes[l];
+  const uint64_t total = slots * nblk * kch * T_NDIG * 8;
+  tm_pack_db_kernel<<<sm_count() * 16, 256, 0, stream>>>(pp, total);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_cuda_error(e);
+  e = cudaStreamSynchronize(stream);
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+// One RowSel problem through the tensor-memory kernel. pair: the SM-pair
+// form; GPIR_ENOTSUP when the batch has an odd number of 32-row m-blocks or no
+// CTA pair can be resident.
+int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
+                   uint32_t lookahead_mb, bool pair, cudaStream_t stream) {
+  if (!db->db_digits12) return GPIR_ENOTSUP;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (dev < 0 || dev >= 64) return GPIR_EINVAL;
+  const uint32_t M = 2 * batch;
+  const uint32_t mblk = (M + T_MROWS - 1) / T_MROWS;
+  if (pair && (mblk & 1u)) return GPIR_ENOTSUP;
+  {
+    std::lock_guard<std::mutex> lk(g_tm_mu);
+    if (!g_tm_attr_done[dev]) {
+      e = cudaFuncSetAttribute(tc_tmem_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)TmemCfg<false>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_tmem_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TmemCfg<false>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_tmem_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TmemCfg<true>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_tmem_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TmemCfg<true>::SMEM);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      cudaLaunchAttribute attr[1];
+      const cudaLaunchConfig_t cfg = tm_pair_config((unsigned)(sm_count() / 2 * 2), nullptr, attr);
+      int n = 0;
+      e = cudaOccupancyMaxActiveClusters(&n, tc_tmem_kernel<false, true>, &cfg);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+      g_tm_pairs[dev] = n > 0 ? n : -1;
+      g_tm_attr_done[dev] = true;
+    }
+  }
+  if (pair && g_tm_pairs[dev] < 0) return GPIR_ENOTSUP;
+  const gpir_params &prm = db->params;
+  const uint32_t L = prm.num_limbs, N = prm.n;
+  TmemParams tp;
+  memset(&tp, 0, sizeof(tp));
+  tp.L = L;
+  tp.N = N;
+  tp.M = M;
+  tp.d0 = db->d0;
+  tp.d1 = db->d1;
+  tp.mblk = mblk;
+  tp.nblk = (db->d1 + T_NCOLS - 1) / T_NCOLS;
+  tp.kch = (db->d0 + T_KCHUNK - 1) / T_KCHUNK;
+  tp.gpl = (N + 7) / 8;
+  tp.n_entries = (uint64_t)tp.gpl * L * mblk;
+  tp.spg = N < 8 ? N : 8u;
+  tp.upe = (uint64_t)tp.spg * tp.nblk;
+  tp.n_units = (pair ? tp.n_entries / 2 : tp.n_entries) * tp.upe;
+  tp.n_tasks = tp.n_entries * tp.kch;
+  const size_t entry_bytes = (size_t)8 * tp.kch * T_RAW_TILE;
+  uint64_t R = ring_target / entry_bytes;
+  if (R < 2) R = 2;
+  if (pair && (R & 1)) ++R;   // both entries of a pair unit share R's parity classes
+  if (R > tp.n_entries) R = tp.n_entries;
+  tp.R = (uint32_t)R;
+  const size_t ring_bytes = (size_t)R * entry_bytes;
+  const size_t flag_bytes = ((size_t)8 * R + 16 + 8 + 8 * kNumTmemCounters + 255) & ~(size_t)255;
+  uint8_t *ws = nullptr;
+  int rc = tc_stream_workspace(stream, ring_bytes + flag_bytes, &ws);
+  if (rc != GPIR_OK) return rc;
+  tp.ring = ws;
+  uint8_t *flags = ws + ring_bytes;
+  tp.ctr = reinterpret_cast<unsigned long long *>(flags);
+  tp.ready = reinterpret_cast<uint32_t *>(flags + 16);
+  tp.consumed = tp.ready + R;
+  tp.prof = trace_enabled()
+                ? reinterpret_cast<unsigned long long *>(((uintptr_t)(tp.consumed + R) + 7) & ~(uintptr_t)7)
+                : nullptr;
+  e = cudaMemsetAsync(flags, 0, flag_bytes, stream);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  {
+    const uint64_t dims[5] = {N, L, 2, db->d0, batch};
+    const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
+                             (uint64_t)db->d0 * 2 * L * N * 4};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)T_KCHUNK, (uint32_t)(T_MROWS / 2)};
+    rc = encode_tiled_u32(&tp.ct_map, ct, 5, dims, str, box);
+    if (rc != GPIR_OK) return rc;
+  }
+  tp.b_tiles = db->db_digits12;
+  tp.out = out;
+  tp.lookahead =
+      lookahead_mb == 0 ? 0u : (uint32_t)std::max<uint64_t>(2, ((uint64_t)lookahead_mb << 20) / entry_bytes);
+  tp.err = device_error_word();
+  for (uint32_t l = 0; l < L; ++l) tp.limb[l] = make_tm_limb(prm.primes[l]);
+  if (pair) {
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = tm_pair_config((unsigned)(2 * g_tm_pairs[dev]), stream, attr);
+    const int tr = trace_begin("tc_tmem_pair", stream);
+    e = tp.prof ? cudaLaunchKernelEx(&cfg, tc_tmem_kernel<true, true>, tp)
+                : cudaLaunchKernelEx(&cfg, tc_tmem_kernel<false, true>, tp);
+    trace_end(tr, stream);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (tp.prof) trace_counters(tp.prof, kNumTmemCounters, stream);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+  }
+  const int tr = trace_begin("tc_tmem", stream);
+  if (tp.prof)
+    tc_tmem_kernel<true, false><<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
+  else
+    tc_tmem_kernel<false, false><<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
+  trace_end(tr, stream);
+  if (tp.prof) trace_counters(tp.prof, kNumTmemCounters, stream);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+}  // namespace gpir

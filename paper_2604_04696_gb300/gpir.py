@@ -300,12 +300,18 @@ FUSED_COUNTERS = ["producer_wait_ready", "producer_wait_empty", "mma_wait_full",
                   "ingest_busy", "ingest_wait_slabs", "ingest_push", "cta_cycles"]
 
 
-def gpir_trace_counters():
-    """{name: cycles} of the last fused tensor-core launch made with tracing on."""
+TMEM_COUNTERS = ["p_wait_ready", "p_wait_empty", "c_wait_full", "c_busy", "m_wait_a", "m_wait_acc",
+                 "e_wait_acc", "e_busy", "i_wait_slot", "i_wait_box", "i_busy", "i_fence", "cta_cycles"]
+
+
+def gpir_trace_counters(names=None):
+    """{name: cycles} of the last traced fused, cluster or tensor-memory launch
+    (names: FUSED_COUNTERS, the default, or TMEM_COUNTERS)."""
+    names = FUSED_COUNTERS if names is None else names
     buf = (ctypes.c_ulonglong * 16)()
     n = ctypes.c_uint32(0)
     _check(lib.gpir_trace_counters(buf, 16, ctypes.byref(n)), "gpir_trace_counters")
-    return {FUSED_COUNTERS[i] if i < len(FUSED_COUNTERS) else str(i): int(buf[i]) for i in range(n.value)}
+    return {names[i] if i < len(names) else str(i): int(buf[i]) for i in range(n.value)}
 
 
 def gpir_strerror(code):

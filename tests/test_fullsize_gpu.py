@@ -26,8 +26,9 @@ import synth
 pytestmark = pytest.mark.gpu
 
 # (path, tile variant): the tensor-core fused kernel with and without the
-# ingest lookahead, its SM-pair form, and the CUDA-core path's default tiles.
-RUNS = [(4, 0), (4, 3), (4, 7), (1, None)]
+# ingest lookahead, its SM-pair form, the tensor-memory kernel (12 digit
+# products) and its SM-pair form, and the CUDA-core path's default tiles.
+RUNS = [(4, 0), (4, 3), (4, 7), (4, 8), (4, 9), (1, None)]
 
 
 @pytest.fixture(scope="module")

@@ -81,6 +81,52 @@ def test_every_variant(g, path, B):
     _check_full(g, B, 70, 40, 2, 64, synth.PRIMES_28, 77 + B, p, variants=list(range(nv)))
 
 
+TMEM_VARIANTS = [8, 9]    # tensor-memory kernel (12 digit products): single CTA, SM pair
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "B%d_D0%d_D1%d_L%d_N%d" % s[:5])
+def test_tmem_kernel_vs_oracle(g, shape):
+    """The tensor-memory kernel (A operand in tensor memory, centred digits,
+    12 products per modular MAC) on every parity shape, both forms."""
+    B, D0, D1, L, N, primes = shape
+    _check_full(g, B, D0, D1, L, N, primes, 2000 + B + D0, PATHS["tc"], variants=TMEM_VARIANTS)
+
+
+@pytest.mark.parametrize("B", [16, 33])
+@pytest.mark.parametrize("xy", [("q-1056832", "q-524800"), ("133160903", "q-524800"), ("h", "h+1"),
+                                ("q-1", "q-1")])
+def test_tmem_extreme_digits_reach_the_bound(g, B, xy):
+    """Residues whose centred digits sit at the ends of their ranges, over
+    D0 = 2048 rows (four 512-row groups): ciphertext q - 1056832 (digits -64,
+    -64, -64, 0) against database q - 524800 (digits -512, -512, 0) drives the
+    group sums of 6 of the 12 digit pairs to exactly 2^24; 133160903 puts the
+    top ciphertext digit at +64. Result D0 * x * y mod q everywhere. B = 16
+    gives one 32-row m-block (single-CTA form even for the pair variant), B =
+    33 three (pairs plus a single)."""
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    _skip_unbuilt(g, PATHS["tc"])
+    primes = synth.PRIMES_28
+    D0, D1, L, N = 2048, 72, 2, 32
+    val = {"q-1056832": lambda q: q - 1056832, "q-524800": lambda q: q - 524800, "133160903": lambda q: 133160903,
+           "h": lambda q: (q - 1) // 2, "h+1": lambda q: (q + 1) // 2, "q-1": lambda q: q - 1}
+    fx, fy = val[xy[0]], val[xy[1]]
+    ct = np.empty((B, D0, 2, L, N), dtype=np.uint32)
+    db = np.empty((D0, D1, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        ct[:, :, :, l] = fx(q)
+        db[:, :, l] = fy(q)
+    h = DbHandle(g, db, N, primes, path_mask=PATHS["tc"])
+    try:
+        ct_d = to_dev(ct)
+        for v in TMEM_VARIANTS:
+            g.gpir_set_variant(h.h, B, PATHS["tc"], v)
+            got = to_host(h.rowsel(ct_d, B, PATHS["tc"]))
+            for l, q in enumerate(primes):
+                assert np.all(got[:, :, :, l] == (D0 * fx(q) * fy(q)) % q), (v, l)
+    finally:
+        h.close()
+
+
 @pytest.mark.parametrize("path", PATH_LIST)
 def test_worst_case_accumulation(g, path):
     """All residues q-1 with D0 = 2048: every product is maximal; result D0 mod q."""

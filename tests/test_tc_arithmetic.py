@@ -308,3 +308,166 @@ def test_cuda_core_model_equals_oracle():
     ct_w = np.broadcast_to(qm[None, None, None, :, None] - 1, ct.shape).copy()
     db_w = np.broadcast_to(qm[None, None, :, None] - 1, db.shape).copy()
     assert np.array_equal(cc_model_rowsel(ct_w, db_w, primes), oracle.rowsel(ct_w, db_w, primes))
+
+
+# ---------------------------------------------------------------------------
+# The tensor-memory kernel's arithmetic: 12 digit products per modular MAC.
+#
+# Both operands are first centred: x -> x - q when x > (q-1)/2, congruent mod
+# q and of magnitude below 2^27, so the product mod q is unchanged. Then
+#   - ciphertext residues: y = x~ + O_A, O_A = 64 (1 + 2^7 + 2^14 + 2^21),
+#     carried through the digit ring as z, the four 7-bit fields of y spread
+#     one per byte (byte u = (y >> 7u) & 127, byte 3 = y >> 21 <= 128; bit 7 of
+#     bytes 0..2 is don't-care); digit d_u = field_u - 64 in [-64, 64];
+#   - database residues: Y = v~ + O_B, O_B = 512 (1 + 2^10), digits
+#     e_0 = (Y & 1023) - 512, e_1 = ((Y >> 10) & 1023) - 512, e_2 = Y >> 20
+#     (arithmetic shift), e_v in [-512, 511] x [-128, 128];
+#   - |d_u e_v| <= 2^15, so a group of 512 rows sums to at most 2^24: exact in
+#     the fp32 accumulator; 12 group sums D_uv per output, recombined as
+#     sum_uv D_uv (2^(7u + 10v) mod q) in 64 bits (< 2^55.6 per group), four
+#     groups added (< 2^57.6) before one Barrett reduction of sum + off58.
+# The fp16 digit of a byte is built as (0x6400 | field) - 1088 in fp16, which
+# is exactly field - 64; the model does that in numpy float16.
+# ---------------------------------------------------------------------------
+
+O_A = 64 * (1 + (1 << 7) + (1 << 14) + (1 << 21))
+O_B = 512 * (1 + (1 << 10))
+GROUP12 = 512
+FLUSH12 = 4
+
+
+def ct_fields(x, q):
+    """The ring encoding z of ciphertext residues x (uint32 array), bit for bit
+    as the kernel's shift-and-merge sequence computes it."""
+    x = np.asarray(x, dtype=np.uint32)
+    h = np.uint32((q - 1) // 2)
+    y = (x + np.uint32(O_A) - np.where(x > h, np.uint32(q), np.uint32(0))).astype(np.uint32)
+    z = (y & np.uint32(0x7F)) | ((y << np.uint32(1)) & np.uint32(0xFFFFFF80))
+    z = (z & np.uint32(0x7FFF)) | ((y << np.uint32(2)) & np.uint32(0xFFFF8000))
+    z = (z & np.uint32(0x7FFFFF)) | ((y << np.uint32(3)) & np.uint32(0xFF800000))
+    return z
+
+
+def ct_digit_fp16(z, u):
+    """Digit u of ring words z as the kernel builds it: the byte (7 bits, all 8
+    for the top digit) under 0x6400 as an fp16, then one fp16 addition of -1088."""
+    mask = 0x7F if u < 3 else 0xFF
+    bits = ((z >> np.uint32(8 * u)) & np.uint32(mask)).astype(np.uint16) | np.uint16(0x6400)
+    return (bits.view(np.float16) + np.float16(-1088.0)).astype(np.float16)
+
+
+def db_digits12(v, q):
+    """[..., 3] digits e_v of database residues (int64)."""
+    v = np.asarray(v, dtype=np.int64)
+    vt = np.where(v > (q - 1) // 2, v - q, v)
+    Y = vt + O_B
+    return np.stack([(Y & 1023) - 512, ((Y >> 10) & 1023) - 512, Y >> 20], axis=-1)
+
+
+def tmem_model_rowsel(ct, db, primes, group=GROUP12, flush=FLUSH12, check_bounds=True):
+    ct = np.asarray(ct)
+    db = np.asarray(db)
+    B, D0, _, L, T = ct.shape
+    D1 = db.shape[1]
+    out = np.zeros((B, D1, 2, L, T), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        q = int(q)
+        w = np.array([[pow(2, 7 * u + 10 * v, q) for v in range(3)] for u in range(4)], dtype=np.int64)
+        off58 = -(-(1 << 58) // q) * q
+        for t in range(T):
+            z = ct_fields(ct[:, :, :, l, t].transpose(0, 2, 1).reshape(2 * B, D0), q)      # [2B][D0]
+            a = [ct_digit_fp16(z, u).astype(np.float32) for u in range(4)]
+            e = db_digits12(db[:, :, l, t], q).astype(np.float32)                             # [D0][D1][3]
+            res = np.zeros((2 * B, D1), dtype=np.int64)
+            acc = np.zeros((2 * B, D1), dtype=np.int64)
+            groups = 0
+            for g0 in range(0, D0, group):
+                g1 = min(D0, g0 + group)
+                for u in range(4):
+                    for v in range(3):
+                        D = a[u][:, g0:g1] @ e[g0:g1, :, v]                      # fp32 products and sums
+                        if check_bounds:
+                            assert np.all(np.abs(D) <= 2 ** 24)
+                        acc += D.astype(np.int64) * w[u, v]
+                groups += 1
+                if groups == flush or g1 == D0:
+                    if check_bounds:
+                        assert np.all(np.abs(acc) < 2 ** 58)
+                    res = (res + (acc + off58) % q) % q
+                    acc[:] = 0
+                    groups = 0
+            out[:, :, :, l, t] = res.reshape(B, 2, D1).transpose(0, 2, 1).astype(np.uint32)
+    return out
+
+
+def test_ring_encoding_and_fp16_digits_reconstruct_the_centred_residue():
+    rng = np.random.default_rng(17)
+    for q in list(PRIMES) + [17, 97, 268042241]:
+        h = (q - 1) // 2
+        x = np.concatenate([rng.integers(0, q, 4000), [0, 1, h, h + 1, q - 1, q - 1056832, q - 2]]).astype(np.uint32)
+        x = x[x < q]
+        z = ct_fields(x, q)
+        d = np.stack([ct_digit_fp16(z, u).astype(np.int64) for u in range(4)], axis=-1)
+        assert d.min() >= -64 and d.max() <= 64
+        xt = np.where(x.astype(np.int64) > h, x.astype(np.int64) - q, x.astype(np.int64))
+        assert np.array_equal((d * np.array([1, 1 << 7, 1 << 14, 1 << 21])).sum(-1), xt)
+        e = db_digits12(x, q)
+        assert e[..., :2].min() >= -512 and e[..., :2].max() <= 511 and np.abs(e[..., 2]).max() <= 128
+        assert np.array_equal((e * np.array([1, 1 << 10, 1 << 20])).sum(-1), xt)
+    # every digit and its fp16 image exact: the fp16 arithmetic equals the integer one
+    z = np.arange(0, 1 << 16, dtype=np.uint32) * np.uint32(0x01010101 // 257 + 1)
+    for u in range(4):
+        f = (z >> np.uint32(8 * u)) & np.uint32(0x7F if u < 3 else 0xFF)
+        assert np.array_equal(ct_digit_fp16(z, u).astype(np.int64), f.astype(np.int64) - 64)
+
+
+def test_tmem_model_matches_oracle_random():
+    primes = PRIMES
+    B, D0, D1, L, T = 3, 1100, 9, 2, 2          # three groups, the last one ragged
+    ct = synth.ct_tensor(301, B, D0, L, T, primes)
+    db = synth.db_tensor(301, D0, D1, L, T, primes)
+    assert np.array_equal(tmem_model_rowsel(ct, db, primes), oracle.rowsel(ct, db, primes))
+
+
+def test_tmem_model_extreme_digits_reach_the_bound():
+    """Residues whose digits sit at the ends of their ranges: ciphertext
+    q - 1056832 (centred -1056832: digits -64, -64, -64, 0) against database
+    q - 524800 (centred -524800: digits -512, -512, 0), so the group sums of
+    the (u < 3, v < 2) pairs reach exactly 2^24; and the top ciphertext digit at
+    +64 against -512. The model stays exact and equals D0 * x * y mod q."""
+    primes = PRIMES
+    B, D0, D1, L, T = 1, 2048, 2, 2, 1
+    for (xs, ys) in [((lambda q: q - 1056832), (lambda q: q - 524800)),
+                     ((lambda q: 133160896 + 7), (lambda q: q - 524800)),
+                     ((lambda q: (q - 1) // 2), (lambda q: (q + 1) // 2))]:
+        ct = np.empty((B, D0, 2, L, T), dtype=np.uint32)
+        db = np.empty((D0, D1, L, T), dtype=np.uint32)
+        for l, q in enumerate(primes):
+            ct[:, :, :, l] = xs(q)
+            db[:, :, l] = ys(q)
+        got = tmem_model_rowsel(ct, db, primes)
+        for l, q in enumerate(primes):
+            assert np.all(got[:, :, :, l] == (D0 * xs(q) * ys(q)) % q)
+    q = primes[0]
+    z = ct_fields(np.array([q - 1056832], dtype=np.uint32), q)
+    assert [int(ct_digit_fp16(z, u)[0]) for u in range(4)] == [-64, -64, -64, 0]
+    assert db_digits12(np.array([q - 524800]), q).tolist() == [[-512, -512, 0]]
+    z = ct_fields(np.array([133160896 + 7], dtype=np.uint32), q)
+    assert int(ct_digit_fp16(z, 3)[0]) == 64
+
+
+def test_tmem_model_negative_control_group_too_long():
+    """With 1025-row groups a partial sum passes 2^24 and fp32 rounds it: the
+    model (bounds unchecked) then differs from the oracle, so the 512-row
+    limit is what keeps the arithmetic exact."""
+    primes = PRIMES[:1]
+    q = primes[0]
+    B, D0, D1, L, T = 1, 1025, 1, 1, 1
+    ct = np.full((B, D0, 2, L, T), q - 1056832, dtype=np.uint32)
+    db = np.full((D0, D1, L, T), q - 524800, dtype=np.uint32)
+    ct[:, -1] = 1          # one more product of 1 after the sums reached 2^24 + ...
+    db[-1] = 1
+    want = oracle.rowsel(ct, db, primes)
+    assert np.array_equal(tmem_model_rowsel(ct, db, primes), want)            # 512-row groups: exact
+    bad = tmem_model_rowsel(ct, db, primes, group=1025, check_bounds=False)
+    assert not np.array_equal(bad, want)
