@@ -594,10 +594,11 @@ def run_pir_pipeline(g, torch, steps=5, warmup=3):
             "ms": ms, "queries_s": B / (ms / 1e3), "phase_ms": {k: round(v, 4) for k, v in phase.items()}}
 
 
-def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
+def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4, repeats=3):
     """The serving workload: three resident DBs (N=4096, 2 limbs; 256x64,
     512x64, 1024x128), Poisson arrivals at each rate, every query a toy-RLWE
-    one-hot selection drawn from a per-DB pool; p50/p99 latency and queries/s."""
+    one-hot selection drawn from a per-DB pool; p50/p99 latency and queries/s,
+    each the median of `repeats` runs (every run listed)."""
     from paper_2604_04696_gb300.server import Request, ResidentDb, Server, poisson_arrivals
     from synth.device import toy_rlwe_query
     import gc
@@ -629,16 +630,21 @@ def run_serving(g, torch, rates=(200, 500, 1000, 2000), seconds=1.5, seed=4):
     srv.run(warm)
     out = []
     for rate in rates:
-        n = max(50, int(rate * seconds))
-        arr = poisson_arrivals(float(rate), n, seed=seed + rate)
-        reqs = []
-        for i, t in enumerate(arr):
-            d = int(rng.integers(0, 3))
-            reqs.append(Request(i, d, pools[d][int(rng.integers(0, 4))], float(t)))
-        st = srv.run(reqs)
-        out.append({"offered_qps": rate, "queries_s": st["queries_s"], "p50_ms": st["p50_ms"],
-                    "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "requests": st["requests"],
-                    "rejected": st["rejected"]})
+        reps = []
+        for rep in range(repeats):
+            n = max(50, int(rate * seconds))
+            arr = poisson_arrivals(float(rate), n, seed=seed + rate + 1000 * rep)
+            reqs = []
+            for i, t in enumerate(arr):
+                d = int(rng.integers(0, 3))
+                reqs.append(Request(i, d, pools[d][int(rng.integers(0, 4))], float(t)))
+            reps.append(srv.run(reqs))
+        med = lambda k: float(np.median([r[k] for r in reps]))
+        out.append({"offered_qps": rate, "queries_s": med("queries_s"), "p50_ms": med("p50_ms"),
+                    "p99_ms": med("p99_ms"), "mean_batch": med("mean_batch"),
+                    "requests": int(sum(r["requests"] for r in reps)), "rejected": int(sum(r["rejected"] for r in reps)),
+                    "repeats": [{"p50_ms": round(r["p50_ms"], 3), "p99_ms": round(r["p99_ms"], 3),
+                                 "queries_s": round(r["queries_s"], 1)} for r in reps]})
     for d in dbs:
         g.gpir_db_free(d.h)
     g.gpir_params_destroy(params)

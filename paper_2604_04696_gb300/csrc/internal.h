@@ -124,7 +124,7 @@ void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 // and one launch (pair: the SM-pair form; GPIR_ENOTSUP if it does not apply).
 int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream);
 int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                   uint32_t lookahead_mb, bool pair, cudaStream_t stream);
+                   uint32_t lookahead_mb, uint32_t hints, bool pair, cudaStream_t stream);
 // The tensor-core workspace kept for (current device, stream), grown on demand
 // (never inside a stream capture: GPIR_ENOMEM then).
 int tc_stream_workspace(cudaStream_t stream, size_t need, uint8_t **out);

@@ -1955,6 +1955,8 @@ constexpr FusedVariant kFusedVariants[] = {
     {kKindPair, 48, 0, 16},             // 7: SM pairs (cta_group::2) sharing each database tile
     {kKindTmem, 48, 0, 16},             // 8: A operand in tensor memory, 12 digit products
     {kKindTmemPair, 48, 0, 16},         // 9: its SM-pair form
+    {kKindTmem, 48, 1, 16},             // 10: 8 with raw boxes evict-first, ring stores evict-last
+    {kKindTmemPair, 48, 1, 16},         // 11: 9 with those hints
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));
 
@@ -2225,10 +2227,10 @@ int rowsel_tc_launch(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint
   }
   if (v.kind == kKindTmem || v.kind == kKindTmemPair) {
     const bool pr = v.kind == kKindTmemPair;
-    const int rc = tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, pr, stream);
+    const int rc = tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, v.hints, pr, stream);
     if (rc != GPIR_ENOTSUP || !pr) return rc;
     // an odd number of m-blocks (or no pair fits): the single-CTA form
-    return tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, false, stream);
+    return tc_launch_tmem(db, batch, ct, out, (size_t)v.ring_mb << 20, v.lookahead_mb, v.hints, false, stream);
   }
   if (v.kind == kKindPair) {
     const int rc = tc_launch_fused(db, batch, ct, out, (size_t)v.ring_mb << 20, v.hints, v.lookahead_mb, true, stream);

@@ -65,27 +65,39 @@ constexpr int T_KGROUP = 8;                          // k-chunks per exact group
 constexpr int T_FLUSH = 4;                           // groups summed before one reduction
 constexpr int T_RAW_TILE = T_MROWS * T_KCHUNK * 4;   // 8 KB ring tile
 constexpr int T_B_TILE = T_NDIG * T_KCHUNK * 2;      // 24 KB
-constexpr int T_STAGES = 4;
+constexpr int T_ABUF = 4;                           // tensor-memory A buffers (32 columns each)
+constexpr uint32_t T_PREF = 8;                       // L2 prefetch distance, in k-chunks
 constexpr uint32_t T_ACC_COLS = T_NDIG;
 constexpr uint32_t T_A_COL0 = 2 * T_ACC_COLS;        // 384
 constexpr uint32_t T_TMEM_COLS = 512;
 constexpr uint32_t kOffA = 64u * (1u + (1u << 7) + (1u << 14) + (1u << 21));
 constexpr int32_t kOffB = 512 * (1 + (1 << 10));
 
-// Warp roles (640 threads).
-constexpr int W_PROD = 0, W_MMA = 1, W_STORE = 2;
-constexpr int W_CONV0 = 4;                           // 4 converter warps: lane quarters 0..3
-constexpr int W_EPI0 = 8, N_EPI = 8;                 // 8 epilogue warps: quarter = warp & 3, column half
-constexpr int W_ING0 = 16, N_ING = 4;                // 4 ingest warps
-constexpr int T_THREADS = 32 * (W_ING0 + N_ING);     // 640
+// Warp roles (896 threads). Tensor-memory lane quarter of a warp = warp % 4.
+constexpr int W_PROD = 0, W_MMA = 1, W_STORE = 2;    // warp 3 idles
+constexpr int W_CONV0 = 4, N_CONV = 8;               // two converter sets of 4 warps (quarters 0..3),
+                                                     // set s converts stages s and s + 2
+constexpr int W_EPI0 = 12, N_EPI = 8;                // 8 epilogue warps: quarter, column half
+constexpr int W_ING0 = 20, N_ING = 8;                // 8 ingest warps
+constexpr int T_THREADS = 32 * (W_ING0 + N_ING);     // 896
+static_assert(W_CONV0 % 4 == 0 && W_EPI0 % 4 == 0, "tensor-memory roles start on a lane quarter 0 warp");
 constexpr int T_RAW_BOX = 16 * T_KCHUNK * 2 * 8 * 4; // 64 KB: 16 clients x 64 k x 2 x 8 slots
 constexpr int T_OUT_BYTES = T_MROWS * T_NCOLS * 4;   // 8 KB
 
+// Shared-memory stages (B tile part + ring tile) are decoupled from the four
+// tensor-memory A buffers: k-chunk i of a CTA uses stage i % NS and A buffer
+// i % T_ABUF, so the SM-pair form, whose stages are smaller, runs a deeper
+// copy pipeline.
 template <bool PAIR>
 struct TmemCfg {
   static constexpr int B_BYTES = PAIR ? T_B_TILE / 2 : T_B_TILE;   // this CTA's part of B
   static constexpr int STAGE = T_RAW_TILE + B_BYTES;
-  static constexpr size_t SMEM = 1024 + (size_t)T_STAGES * STAGE + T_RAW_BOX + T_OUT_BYTES + 512;
+  static constexpr int NS = PAIR ? 6 : 4;
+  static constexpr size_t SMEM = 1024 + (size_t)NS * STAGE + T_RAW_BOX + T_OUT_BYTES + 768;
+  // Even: a converter set waits full[stage] for k-chunks i, i + 2, ...; the
+  // stage's previous k-chunk i - NS must then be one the same set has already
+  // waited for, else a parity wait could pass on the phase before it.
+  static_assert(NS % 2 == 0, "two converter sets need an even number of stages");
 };
 static_assert(TmemCfg<false>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
 static_assert(TmemCfg<true>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
@@ -100,6 +112,7 @@ struct TmLimb {
 struct TmemParams {
   uint32_t L, N, M, d0, d1, mblk, nblk, kch;
   uint32_t R, gpl, spg, lookahead;
+  uint32_t hints;                       // 1: raw boxes evict-first, ring stores evict-last in L2
   uint64_t n_entries, upe, n_units, n_tasks;
   const uint16_t *b_tiles;              // [slot][nblk][kch] x 24 KB
   uint32_t *out;
@@ -119,7 +132,8 @@ enum TmemCounter {
   kTPWaitReady = 0,   // producer: ring entry not yet ingested
   kTPWaitEmpty,       // producer: no free stage
   kTCWaitFull,        // converter: stage not landed
-  kTCBusy,            // converter: converting and storing to tensor memory
+  kTCBusy,            // converter: shared-memory loads and digit conversion
+  kTCStore,           // converter: tensor-memory store, its wait and the signal
   kTMWaitA,           // MMA: A buffer not converted
   kTMWaitAcc,         // MMA: accumulator not drained
   kTEWaitAcc,         // epilogue: MMAs of the group not done
@@ -169,15 +183,19 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       : "memory");
 }
 
-// Three loads of 8 columns each (the three database digits of 8 columns).
-__device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t (&r)[24]) {
+// Prefetch [src, src + bytes) into L2 (bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Three loads of 4 columns each (the three database digits of 4 columns).
+__device__ __forceinline__ void tmem_ld4x3(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t (&r)[12]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%12];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%13];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%14];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
       : "r"(t0), "r"(t1), "r"(t2));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -276,18 +294,21 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage st: B part at smem + st * STAGE (1024-aligned), ring tile after it
-  uint8_t *rawbox = smem + T_STAGES * Cfg::STAGE;
+  constexpr int NS = Cfg::NS;
+  uint8_t *rawbox = smem + NS * Cfg::STAGE;
   uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + T_RAW_BOX);
   uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + T_RAW_BOX + T_OUT_BYTES);
-  uint64_t *empty = full + T_STAGES;
-  uint64_t *afull = empty + T_STAGES;             // A buffer st converted (and, pair: both CTAs')
-  uint64_t *acc_full = afull + T_STAGES;
+  uint64_t *empty = full + NS;
+  uint64_t *afull = empty + NS;                   // [T_ABUF] A buffer converted (pair: both CTAs')
+  uint64_t *aempty = afull + T_ABUF;              // [T_ABUF] A buffer read by its MMAs
+  uint64_t *acc_full = aempty + T_ABUF;
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *box_bar = acc_empty + 2;
   uint64_t *ostage_full = box_bar + 1;
   uint64_t *ostage_empty = ostage_full + 1;
-  uint64_t *stage_unit = ostage_empty + 1;        // [T_STAGES]
-  uint64_t *acc_unit = stage_unit + T_STAGES;     // [2]
+  uint64_t *stage_unit = ostage_empty + 1;        // [NS]
+  uint64_t *stage_kc = stage_unit + NS;           // [NS] k-chunk of the unit in the stage
+  uint64_t *acc_unit = stage_kc + NS;             // [2]
   uint64_t *task_slot = acc_unit + 2;
   uint64_t *ostage_unit = task_slot + 1;
   uint64_t *mail = ostage_unit + 1;               // pair: [4] claimed units, even -> odd CTA
@@ -299,11 +320,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < T_STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-      // single CTA: the 4 converter warps; pair (even CTA): both CTAs' converter warps
-      mbar_init(&afull[s], (PAIR && rank == 0) ? 8 : 4);
+    for (int s2 = 0; s2 < NS; ++s2) {
+      mbar_init(&full[s2], 1);
+      mbar_init(&empty[s2], 1);
+    }
+    for (int a = 0; a < T_ABUF; ++a) {
+      // single CTA: the 4 converter warps of a set; pair (even CTA): both CTAs' warps
+      mbar_init(&afull[a], (PAIR && rank == 0) ? 8 : 4);
+      mbar_init(&aempty[a], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 2);
@@ -414,133 +438,188 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
 
   if (warp == W_PROD) {
     // ---------------- producer: claims units, copies ring + B tiles ----------------
+    // Claims one unit ahead and prefetches into L2 the tiles T_PREF stages
+    // ahead (the rest of this unit, then the next unit's), so that the bulk
+    // copies on the critical path hit L2.
     if (lane == 0) {
       uint32_t st = 0, ph = 0, mi = 0;
       bool ok = true;
-      for (;;) {
-        uint64_t u;
+      auto claim = [&](uint64_t &u) -> bool {
         if constexpr (PAIR) {
           const uint32_t ms = mi & 3u, mph = (mi >> 2) & 1u;
           ++mi;
           if (rank == 0) {
             u = atomicAdd(&p.ctr[0], 1ull);
             if (u >= p.n_units) u = kNoUnit;
-            if (!(ok = wait(&mail_empty[ms], mph ^ 1u, kErrQueueWait))) break;
+            if (!wait(&mail_empty[ms], mph ^ 1u, kErrQueueWait)) return false;
             st_cluster_u64(map_peer(smem_u32(&mail[ms]), 1), u);
             mbar_arrive_remote(map_peer(smem_u32(&mail_full[ms]), 1));
           } else {
-            if (!(ok = wait(&mail_full[ms], mph, kErrQueueWait))) break;
+            if (!wait(&mail_full[ms], mph, kErrQueueWait)) return false;
             u = *reinterpret_cast<volatile uint64_t *>(&mail[ms]);
             mbar_arrive_remote(map_peer(smem_u32(&mail_empty[ms]), 0));
           }
-          if (u == kNoUnit) break;
         } else {
           u = atomicAdd(&p.ctr[0], 1ull);
-          if (u >= p.n_units) break;
+          if (u >= p.n_units) u = kNoUnit;
         }
-        const uint64_t E = entry_of(u);
+        return true;
+      };
+      struct Src {
+        const uint8_t *a, *b;
+        uint64_t E;
+      };
+      auto sources = [&](uint64_t u) -> Src {
+        Src r;
+        r.E = entry_of(u);
         const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-        const uint32_t g = (uint32_t)(E / p.mblk);
+        const uint32_t g = (uint32_t)(r.E / p.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch))))) break;
+        r.a = p.ring + (((r.E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
+        r.b = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
+              (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
+        return r;
+      };
+      uint64_t u = kNoUnit, un = kNoUnit;
+      ok = claim(u);
+      if (ok && u != kNoUnit) ok = claim(un);
+      while (ok && u != kNoUnit) {
+        const Src sc = sources(u);
+        const bool has_next = un != kNoUnit;
+        const Src sn = has_next ? sources(un) : sc;
+        const uint32_t ready_next = (uint32_t)((sn.E / p.R + 1) * p.kch);
+        bool next_ready = false;
+        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[sc.E % p.R], (uint32_t)((sc.E / p.R + 1) * p.kch)))))
+          break;
         fence_proxy_async_global();
-        const uint8_t *a_src = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
-        const uint8_t *b_src = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
-                               (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
         for (uint32_t kc = 0; kc < p.kch; ++kc) {
+          const uint32_t k2 = kc + T_PREF;
+          if (k2 < p.kch) {
+            prefetch_l2(sc.b + (uint64_t)k2 * T_B_TILE, Cfg::B_BYTES);
+            prefetch_l2(sc.a + (uint64_t)k2 * T_RAW_TILE, T_RAW_TILE);
+          } else if (has_next && k2 - p.kch < p.kch) {
+            const uint32_t k3 = k2 - p.kch;
+            prefetch_l2(sn.b + (uint64_t)k3 * T_B_TILE, Cfg::B_BYTES);
+            if (!next_ready) next_ready = ld_acquire(&p.ready[sn.E % p.R]) >= ready_next;
+            if (next_ready) prefetch_l2(sn.a + (uint64_t)k3 * T_RAW_TILE, T_RAW_TILE);
+          }
           if (!(ok = TM_TIMED(kTPWaitEmpty, wait(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
           stage_unit[st] = u;
+          stage_kc[st] = kc;
           uint8_t *sb = smem + st * Cfg::STAGE;
           mbar_arrive_expect_tx(&full[st], Cfg::STAGE);
-          bulk_g2s(sb, b_src + (uint64_t)kc * T_B_TILE, Cfg::B_BYTES, &full[st]);
-          bulk_g2s(sb + Cfg::B_BYTES, a_src + (uint64_t)kc * T_RAW_TILE, T_RAW_TILE, &full[st]);
-          if (++st == T_STAGES) {
+          bulk_g2s(sb, sc.b + (uint64_t)kc * T_B_TILE, Cfg::B_BYTES, &full[st]);
+          bulk_g2s(sb + Cfg::B_BYTES, sc.a + (uint64_t)kc * T_RAW_TILE, T_RAW_TILE, &full[st]);
+          if (++st == NS) {
             st = 0;
             ph ^= 1u;
           }
         }
         if (!ok) break;
+        u = un;
+        un = kNoUnit;
+        if (u != kNoUnit) ok = claim(un);
       }
-      if (ok && wait(&empty[st], ph ^ 1u, kErrTmaWait)) {
-        stage_unit[st] = kNoUnit;   // end of work
+      // end of work: a sentinel in the next two stages, one for each converter set
+      for (int k = 0; k < 2 && ok; ++k) {
+        if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
+        stage_unit[st] = kNoUnit;
         mbar_arrive(&full[st]);
+        if (++st == NS) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (ok) {
         if constexpr (PAIR) {
           // the last multicast commits target this CTA's empty barriers too:
-          // let them land (every stage but the sentinel's) before the CTA leaves
-          for (int s2 = 1; s2 < T_STAGES; ++s2) {
-            if (++st == T_STAGES) {
+          // let them land on the other stages before the CTA leaves
+          for (int s2 = 2; s2 < NS; ++s2) {
+            mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
+            if (++st == NS) {
               st = 0;
               ph ^= 1u;
             }
-            mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
           }
         }
       } else {
-        for (int s2 = 0; s2 < T_STAGES; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
+        for (int s2 = 0; s2 < NS; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
       }
     }
-  } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
+  } else if (warp >= W_CONV0 && warp < W_CONV0 + N_CONV) {
     // ---------------- converters: ring tile (smem) -> fp16 digits -> tensor memory ----------------
     // Thread = tensor-memory lane (row m_hi*32 + u*8 + m_lo of the A operand):
-    // ciphertext row m = m_hi*8 + m_lo of the m-block, digit u.
+    // ciphertext row m = m_hi*8 + m_lo of the m-block, digit u. Set cs
+    // converts stages cs, cs + 2, cs, ... (two sets hide each other's latency).
     const uint32_t qw = (uint32_t)(warp & 3);
+    const uint32_t cs = (uint32_t)(warp - W_CONV0) >> 2;
     const int u = lane >> 3, m_lo = lane & 7;
     const int m = (int)qw * 8 + m_lo;
     const uint32_t lane_base = tmem_base + ((qw * 32u) << 16);
     const uint32_t dsel = (uint32_t)(u | (u << 4) | ((u + 4) << 8) | ((u + 4) << 12));
     const uint32_t dmask = u < 3 ? 0x007F007Fu : 0x00FF00FFu;
-    uint32_t st = 0, ph = 0;
-    uint32_t kc_seen = 0;                 // k-chunks of the current unit seen so far
-    const bool conv_counter = PROF && qw == 0 && lane == 0;
-    for (;;) {
+    const bool conv_counter = PROF && warp == W_CONV0 && lane == 0;
+    for (uint32_t it = 0;; ++it) {
+      const uint32_t i = 2u * it + cs;                      // this CTA's k-chunk sequence number
+      const uint32_t st = i % NS, ph = (i / NS) & 1u;
+      const uint32_t ab = i % T_ABUF, aph = (i / T_ABUF) & 1u;
       const bool okf = conv_counter ? TM_TIMED(kTCWaitFull, wait(&full[st], ph, kErrTmaWait))
                                     : wait(&full[st], ph, kErrTmaWait);
       if (!__all_sync(0xffffffffu, okf)) break;
       const uint64_t tconv = PROF ? clock64() : 0;
       const uint64_t un = stage_unit[st];
       if (un == kNoUnit) {
+        // Wait for the A buffer's previous k-chunk to be read by its MMAs even
+        // here: in the pair form an early sentinel arrival could complete the
+        // even CTA's count-8 afull phase of that previous k-chunk without the
+        // other CTA's arrivals.
+        __all_sync(0xffffffffu, wait(&aempty[ab], aph ^ 1u, kErrMmaWait));
         __syncwarp();
         if (lane == 0) {
           if (PAIR && rank != 0)
-            mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[st]), 0));
+            mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[ab]), 0));
           else
-            mbar_arrive(&afull[st]);
+            mbar_arrive(&afull[ab]);
         }
         break;
       }
-      if (++kc_seen == p.kch) {
-        kc_seen = 0;
-        // the unit's last ring tile is in shared memory: its ring entry may be reused
-        if (qw == 0 && lane == 0) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
-      }
+      // the unit's last ring tile is in shared memory: its ring entry may be reused
+      if (qw == 0 && lane == 0 && stage_kc[st] + 1 == p.kch) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
       const uint4 *row = reinterpret_cast<const uint4 *>(smem + st * Cfg::STAGE + Cfg::B_BYTES) + m * 16;
       uint32_t wv[32];
 #pragma unroll
       for (int c16 = 0; c16 < 16; ++c16) {
         const uint4 z = row[c16 ^ (m & 7)];
-        wv[2 * c16] = digit_pair(z.x, z.y, dsel, dmask);
-        wv[2 * c16 + 1] = digit_pair(z.z, z.w, dsel, dmask);
+        if ((c16 >> 1) & 1) {   // odd k octet: the ring holds its k offsets pairwise swapped
+          wv[2 * c16] = digit_pair(z.y, z.x, dsel, dmask);
+          wv[2 * c16 + 1] = digit_pair(z.w, z.z, dsel, dmask);
+        } else {
+          wv[2 * c16] = digit_pair(z.x, z.y, dsel, dmask);
+          wv[2 * c16 + 1] = digit_pair(z.z, z.w, dsel, dmask);
+        }
       }
-      tmem_st32(lane_base + T_A_COL0 + st * 32u, wv);
+      const uint64_t tst = PROF ? clock64() : 0;
+      if (conv_counter) pc[PROF ? kTCBusy : 0] += tst - tconv;
+      // the digits are in registers; the A buffer's previous k-chunk must have
+      // been read by its MMAs before they overwrite it
+      if (!__all_sync(0xffffffffu, wait(&aempty[ab], aph ^ 1u, kErrMmaWait))) break;
+      tc_fence_after();
+      tmem_st32(lane_base + T_A_COL0 + ab * 32u, wv);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         if (PAIR && rank != 0)
-          mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[st]), 0));
+          mbar_arrive_remote_relaxed(map_peer(smem_u32(&afull[ab]), 0));
         else
-          mbar_arrive(&afull[st]);
+          mbar_arrive(&afull[ab]);
       }
-      if (conv_counter) pc[PROF ? kTCBusy : 0] += clock64() - tconv;
-      if (++st == T_STAGES) {
-        st = 0;
-        ph ^= 1u;
-      }
+      if (conv_counter) pc[PROF ? kTCStore : 0] += clock64() - tst;
     }
   } else if (warp == W_MMA) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      uint32_t st = 0, ph = 0, buf = 0;
+      uint32_t st = 0, ph = 0, buf = 0, ab = 0, abph = 0;
       uint32_t aph[2] = {0, 0};
       bool ok = true;
       const uint32_t kgroups = (p.kch + T_KGROUP - 1) / T_KGROUP;
@@ -549,7 +628,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           // odd CTA: its converters signal the even CTA directly; nothing to issue
           break;
         }
-        if (!(ok = TM_TIMED(kTMWaitA, wait(&afull[st], ph, kErrTmaWait)))) break;
+        if (!(ok = TM_TIMED(kTMWaitA, wait(&afull[ab], abph, kErrTmaWait)))) break;
         const uint64_t u = stage_unit[st];
         if (u == kNoUnit) {
           if ((ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
@@ -572,11 +651,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           const uint32_t c0 = gi * T_KGROUP;
           const uint32_t c1 = min(p.kch, c0 + T_KGROUP);
           for (uint32_t kc = c0; kc < c1; ++kc) {
-            if (!first && !(ok = TM_TIMED(kTMWaitA, wait(&afull[st], ph, kErrTmaWait)))) break;
+            if (!first && !(ok = TM_TIMED(kTMWaitA, wait(&afull[ab], abph, kErrTmaWait)))) break;
             first = false;
             tc_fence_after();
             const uint32_t sb = smem_u32(smem + st * Cfg::STAGE);
-            const uint32_t ta = tmem_base + T_A_COL0 + st * 32u;
+            const uint32_t ta = tmem_base + T_A_COL0 + ab * 32u;
 #pragma unroll
             for (int k16 = 0; k16 < T_KCHUNK / 16; ++k16) {
               const uint32_t acc = (kc > c0 || k16 > 0) ? 1u : 0u;
@@ -585,13 +664,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
               else
                 mma_tmem_a(tmem_d, ta + k16 * 8, sw128_desc(sb + k16 * 32), acc);
             }
-            if constexpr (PAIR)
+            if constexpr (PAIR) {
               mma_commit_pair(&empty[st]);
-            else
+              mma_commit_pair(&aempty[ab]);
+            } else {
               mma_commit(&empty[st]);
-            if (++st == T_STAGES) {
+              mma_commit(&aempty[ab]);
+            }
+            if (++st == NS) {
               st = 0;
               ph ^= 1u;
+            }
+            if (++ab == T_ABUF) {
+              ab = 0;
+              abph ^= 1u;
             }
           }
           if (!ok) break;
@@ -663,31 +749,28 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
       const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t d[24];
-        tmem_ld8x3(tbase + c * 8, tbase + 64 + c * 8, tbase + 128 + c * 8, d);
-        int64_t P[8];
+      for (int c = 0; c < 8; ++c) {
+        uint32_t d[12];
+        tmem_ld4x3(tbase + c * 4, tbase + 64 + c * 4, tbase + 128 + c * 4, d);
+        int64_t P[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
           P[i] = (int64_t)__float2int_rn(__uint_as_float(d[i])) * w0 +
-                 (int64_t)__float2int_rn(__uint_as_float(d[8 + i])) * w1 +
-                 (int64_t)__float2int_rn(__uint_as_float(d[16 + i])) * w2;
+                 (int64_t)__float2int_rn(__uint_as_float(d[4 + i])) * w1 +
+                 (int64_t)__float2int_rn(__uint_as_float(d[8 + i])) * w2;
         // reduce-scatter over the 4 digits u (lanes u*8 + m_lo): thread u keeps
-        // columns c*8 + u and c*8 + 4 + u
+        // column c*4 + u of its half
         const int b0 = u & 1, b1 = (u >> 1) & 1;
-        int64_t K1[4];
+        int64_t K1[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
           const int64_t keep = b0 ? P[2 * i + 1] : P[2 * i];
           const int64_t send = b0 ? P[2 * i] : P[2 * i + 1];
           K1[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
         }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const int64_t keep = b1 ? K1[2 * i + 1] : K1[2 * i];
-          const int64_t send = b1 ? K1[2 * i] : K1[2 * i + 1];
-          acc64[c * 2 + i] += keep + __shfl_xor_sync(0xffffffffu, send, 16);
-        }
+        const int64_t keep = b1 ? K1[1] : K1[0];
+        const int64_t send = b1 ? K1[0] : K1[1];
+        acc64[c] += keep + __shfl_xor_sync(0xffffffffu, send, 16);
       }
       tc_fence_before();
       __syncwarp();
@@ -712,12 +795,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         if (!epi_all(wait(ostage_empty, oph ^ 1u, kErrMmaWait))) break;
         const uint32_t swz = (uint32_t)m_lo << 2;
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            const uint32_t n = half * 32u + c * 8u + i * 4u + (uint32_t)u;
-            out_stage[m_local * T_NCOLS + (n ^ swz)] = res[c * 2 + i];
-          }
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t n = half * 32u + c * 4u + (uint32_t)u;
+          out_stage[m_local * T_NCOLS + (n ^ swz)] = res[c];
+        }
         if (et == 0) *ostage_unit = un;
         __syncwarp();
         if (lane == 0) mbar_arrive(ostage_full);
@@ -755,14 +836,15 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       ph ^= 1u;
     }
   } else if (warp >= W_ING0) {
-    // ---------------- ingest (4 warps, 128 threads) ----------------
+    // ---------------- ingest (8 warps, 256 threads) ----------------
     // Task = (entry E, k-chunk kc): one 64 KB TMA box of 8 slots x 32 rows x
-    // 64 k. Thread it handles items it and it + 128 of the 256 (row, k octet)
-    // items; for each slot it stores the 8 encoded residues of its row and
+    // 64 k. A thread handles (row, k octet, slot half) items; for each slot it
+    // stores the 8 encoded residues of its row and
     // octet as two 16-byte chunks of the slot's ring tile, chunk c16 of row m
     // at position c16 ^ (m % 8) (conflict-free reads by the converters).
     const int it = (warp - W_ING0) * 32 + lane;
     constexpr int NT = 32 * N_ING;
+    const uint64_t pol_last = l2_policy_evict_last();
     uint32_t rph = 0;
     bool issued = false;
     for (;;) {
@@ -784,8 +866,12 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         if (near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
                                                                    (uint32_t)((E / p.R) * p.upe))))) {
           mbar_arrive_expect_tx(box_bar, T_RAW_BOX);
-          tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
-                      (int)(mb * (T_MROWS / 2)));
+          if (p.hints)
+            tma_load_5d_hint(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
+                             (int)(mb * (T_MROWS / 2)), l2_policy_evict_first());
+          else
+            tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
+                        (int)(mb * (T_MROWS / 2)));
           issued = true;
           *task_slot = c;
         } else {
@@ -809,35 +895,44 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       const uint32_t q = p.limb[l].q, h = p.limb[l].h;
       const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox);
       uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
+      // Lane = (k octet j, row parity rp, slot half sh): a warp's 16-byte box
+      // reads at step kk cover all 8 bank groups (4 wavefronts per 512 B, the
+      // minimum) because the thread reads k offset kk ^ (j & 1) and slot half
+      // sh = s4 ^ ((j >> 1) & 1); it stores position kk of its octet's ring
+      // chunk pair from that read, so ring position p of octet j holds k offset
+      // p ^ (j & 1) (the converter swaps the pair for odd octets).
+      const int j = lane >> 2, rp = (lane >> 1) & 1;
+      const int j0 = j & 1, sh = (lane & 1) ^ ((j >> 1) & 1);
 #pragma unroll 1
-      for (int item = it; item < 256; item += NT) {
-        const int m_local = item >> 3, j = item & 7;
-        const int cc = m_local >> 1, rp = m_local & 1;
+      for (int cc = it >> 5; cc < 16; cc += NT / 32) {
+        const int m_local = cc * 2 + rp;
+        uint32_t z[8][4];   // [position kk][slot in half]
 #pragma unroll
-        for (int s4 = 0; s4 < 2; ++s4) {
-          uint32_t z[8][4];   // [kk][slot in half]
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint4 v = raw4[((cc * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh];
+          z[kk][0] = ct_fields(v.x, q, h);
+          z[kk][1] = ct_fields(v.y, q, h);
+          z[kk][2] = ct_fields(v.z, q, h);
+          z[kk][3] = ct_fields(v.w, q, h);
+        }
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint4 v = raw4[((cc * T_KCHUNK + j * 8 + kk) * 2 + rp) * 2 + s4];
-            z[kk][0] = ct_fields(v.x, q, h);
-            z[kk][1] = ct_fields(v.y, q, h);
-            z[kk][2] = ct_fields(v.z, q, h);
-            z[kk][3] = ct_fields(v.w, q, h);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int sl = s4 * 4 + i;
-            if (t0 + sl >= p.N) continue;
-            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
-            uint4 lo, hi;
-            lo.x = z[0][i];
-            lo.y = z[1][i];
-            lo.z = z[2][i];
-            lo.w = z[3][i];
-            hi.x = z[4][i];
-            hi.y = z[5][i];
-            hi.z = z[6][i];
-            hi.w = z[7][i];
+        for (int i = 0; i < 4; ++i) {
+          const int sl = sh * 4 + i;
+          if (t0 + sl >= p.N) continue;
+          uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
+          uint4 lo, hi;
+          lo.x = z[0][i];
+          lo.y = z[1][i];
+          lo.z = z[2][i];
+          lo.w = z[3][i];
+          hi.x = z[4][i];
+          hi.y = z[5][i];
+          hi.z = z[6][i];
+          hi.w = z[7][i];
+          if (p.hints) {
+            st_global_v4_hint(&tile[m_local * 16 + ((2 * j) ^ (m_local & 7))], lo, pol_last);
+            st_global_v4_hint(&tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))], hi, pol_last);
+          } else {
             tile[m_local * 16 + ((2 * j) ^ (m_local & 7))] = lo;
             tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))] = hi;
           }
@@ -953,7 +1048,7 @@ int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream) {
 // form; GPIR_ENOTSUP when the batch has an odd number of 32-row m-blocks or no
 // CTA pair can be resident.
 int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                   uint32_t lookahead_mb, bool pair, cudaStream_t stream) {
+                   uint32_t lookahead_mb, uint32_t hints, bool pair, cudaStream_t stream) {
   if (!db->db_digits12) return GPIR_ENOTSUP;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1039,6 +1134,7 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
   }
   tp.b_tiles = db->db_digits12;
   tp.out = out;
+  tp.hints = hints;
   tp.lookahead =
       lookahead_mb == 0 ? 0u : (uint32_t)std::max<uint64_t>(2, ((uint64_t)lookahead_mb << 20) / entry_bytes);
   tp.err = device_error_word();

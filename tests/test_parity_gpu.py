@@ -81,7 +81,7 @@ def test_every_variant(g, path, B):
     _check_full(g, B, 70, 40, 2, 64, synth.PRIMES_28, 77 + B, p, variants=list(range(nv)))
 
 
-TMEM_VARIANTS = [8, 9]    # tensor-memory kernel (12 digit products): single CTA, SM pair
+TMEM_VARIANTS = [8, 9, 10, 11]    # tensor-memory kernel (12 digit products): single CTA, SM pair, with L2 hints
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "B%d_D0%d_D1%d_L%d_N%d" % s[:5])

@@ -1,0 +1,306 @@
+"""A CPU model of the barrier protocol of the tensor-memory RowSel kernel
+(rowsel_tmem.cu), single-CTA and SM-pair forms, run under random
+interleavings.
+
+The model restates the kernel's rules with exact mbarrier semantics (arrival
+count, transaction bytes, phase parity; no code shared with the CUDA source):
+  - the producer of each CTA claims units one ahead (the pair's odd CTA
+    receives them through a mailbox), fills shared-memory stage i % NS (NS
+    even) for
+    its i-th k-chunk after empty[stage] (arrive.expect_tx on full[stage]; the
+    copies land asynchronously), and ends with a sentinel in two consecutive
+    stages, one per converter set; the pair's producers then wait for the
+    commits of their other stages;
+  - converter set c (two sets of four warps) takes k-chunks i = c, c + 2, ...:
+    waits full[stage], waits aempty[i % NA] (the A buffer's previous k-chunk
+    read by its MMAs; also before a sentinel), stops at a sentinel after
+    arriving on afull, else writes the A buffer and arrives on afull[i % NA]
+    (in the pair, both CTAs' sets arrive on the even CTA's afull, count 8);
+  - the (even CTA's) MMA thread waits afull, issues the k-chunk's MMAs, which
+    read both CTAs' stage and A buffer and accumulate into both CTAs' tensor
+    memory, and commits to empty[stage] and aempty[buffer] (both CTAs in the
+    pair); after each 512-row group it commits to acc_full;
+  - the epilogues drain the accumulators (acc_full / acc_empty, double
+    buffered); the odd CTA also arrives on the even CTA's acc_empty.
+Checked: no deadlock; every MMA reads, in both CTAs, the stage and A buffer of
+its own unit and k-chunk; no A buffer or stage is overwritten before the MMAs
+that read it have run; each epilogue sees every group of every unit once.
+"""
+
+import random
+
+import pytest
+
+NA = 4
+EPI = 8
+
+
+class Bar:
+    def __init__(self, count):
+        self.count = count
+        self.pending = count
+        self.tx = 0
+        self.phase = 0
+
+    def _check(self):
+        if self.pending == 0 and self.tx == 0:
+            self.phase += 1
+            self.pending = self.count
+
+    def arrive(self, n=1, tx=0):
+        self.tx += tx
+        self.pending -= n
+        assert self.pending >= 0, "too many arrivals in one phase"
+        self._check()
+
+    def complete_tx(self, b):
+        self.tx -= b
+        self._check()
+
+    def done(self, parity):
+        return (self.phase & 1) != parity
+
+
+class Cta:
+    def __init__(self, ns, afull_count, acc_empty_count):
+        self.full = [Bar(1) for _ in range(ns)]
+        self.empty = [Bar(1) for _ in range(ns)]
+        self.afull = [Bar(afull_count) for _ in range(NA)]
+        self.aempty = [Bar(1) for _ in range(NA)]
+        self.acc_full = [Bar(2) for _ in range(2)]
+        self.acc_empty = [Bar(acc_empty_count) for _ in range(2)]
+        self.stage = [None] * ns            # data in the stage: (unit, kc) once landed
+        self.stage_unit = [None] * ns
+        self.abuf = [None] * NA             # (unit, kc) converted into A buffer
+        self.acc_unit = [None] * 2
+        self.acc = [None] * 2               # (unit, group) accumulated
+        self.seen = []                      # epilogue log
+
+
+def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
+    rng = random.Random(seed)
+    if pair:
+        ctas = [Cta(ns, 8, 2 * EPI), Cta(ns, 4, EPI)]
+    else:
+        ctas = [Cta(ns, 4, EPI)]
+    mail, mail_full, mail_empty = [None] * 4, [Bar(1) for _ in range(4)], [Bar(1) for _ in range(4)]
+    claims = [0]
+    copies = []
+    engine = []
+    kgroups = (kch + kgroup - 1) // kgroup
+
+    def wait(bar, parity):
+        while not bar.done(parity):
+            yield "blocked"
+
+    def producer(r):
+        cta = ctas[r]
+        st = ph = 0
+        mi = [0]
+
+        def claim():
+            if not pair:
+                u = claims[0] if claims[0] < n_units else None
+                claims[0] += 1
+                return u
+                yield
+            ms, mph = mi[0] % 4, (mi[0] // 4) & 1
+            mi[0] += 1
+            if r == 0:
+                u = claims[0] if claims[0] < n_units else None
+                claims[0] += 1
+                yield from wait(mail_empty[ms], mph ^ 1)
+                mail[ms] = u
+                mail_full[ms].arrive()
+            else:
+                yield from wait(mail_full[ms], mph)
+                u = mail[ms]
+                mail_empty[ms].arrive()
+            return u
+
+        def get():
+            return (yield from claim())
+
+        u = yield from get()
+        un = (yield from get()) if u is not None else None
+        while u is not None:
+            for kc in range(kch):
+                yield from wait(cta.empty[st], ph ^ 1)
+                cta.stage_unit[st] = (u, kc)
+                cta.stage[st] = None
+                cta.full[st].arrive(tx=1)
+                copies.append((cta, st, (u, kc)))
+                st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
+            u, un = un, None
+            if u is not None:
+                un = yield from get()
+        for _ in range(2):
+            yield from wait(cta.empty[st], ph ^ 1)
+            cta.stage_unit[st] = "end"
+            cta.full[st].arrive()
+            st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
+        if pair:
+            for _ in range(2, ns):
+                yield from wait(cta.empty[st], ph ^ 1)
+                st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
+
+    def converter(r, cs):
+        cta = ctas[r]
+        target = ctas[0]          # the pair's odd CTA arrives on the even CTA's afull
+        it = 0
+        while True:
+            i = 2 * it + cs
+            st, ph = i % ns, (i // ns) & 1
+            ab, aph = i % NA, (i // NA) & 1
+            yield from wait(cta.full[st], ph)
+            tag = cta.stage_unit[st]
+            # the A buffer's previous k-chunk must have been read by its MMAs,
+            # also before a sentinel: in the pair, an early sentinel arrival
+            # would complete the even CTA's count-8 afull phase of that
+            # previous k-chunk without the other CTA's arrivals
+            if not (skip_aempty and tag == "end"):
+                yield from wait(cta.aempty[ab], aph ^ 1)
+            if tag == "end":
+                target.afull[ab].arrive(4)
+                return
+            assert cta.stage[st] == tag, "converter read a stage that has not landed"
+            cta.abuf[ab] = tag
+            target.afull[ab].arrive(4)
+            it += 1
+
+    def mma():
+        me = ctas[0]
+        st = ph = buf = ab = abph = 0
+        aph = [0, 0]
+        while True:
+            yield from wait(me.afull[ab], abph)
+            tag = me.stage_unit[st]
+            if tag == "end":
+                yield from wait(me.acc_empty[buf], aph[buf] ^ 1)
+                for c in ctas:
+                    c.acc_unit[buf] = "end"
+                    c.acc_full[buf].arrive(2)
+                return
+            u = tag[0]
+            first = True
+            for gi in range(kgroups):
+                yield from wait(me.acc_empty[buf], aph[buf] ^ 1)
+                for kc in range(gi * kgroup, min(kch, (gi + 1) * kgroup)):
+                    if not first:
+                        yield from wait(me.afull[ab], abph)
+                    first = False
+                    engine.append(("mma", st, ab, (u, kc), buf, gi))
+                    engine.append(("commit", [c.empty[st] for c in ctas] + [c.aempty[ab] for c in ctas]))
+                    st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
+                    ab, abph = (ab + 1) % NA, abph ^ (ab + 1 == NA)
+                for c in ctas:
+                    c.acc_unit[buf] = (u, gi)
+                engine.append(("commit", [c.acc_full[buf] for c in ctas]))
+                for c in ctas:
+                    c.acc_full[buf].arrive()      # the issuing thread's own arrive (remote for the odd CTA)
+                aph[buf] ^= 1
+                buf ^= 1
+
+    def epilogue(r):
+        cta = ctas[r]
+        buf = 0
+        aph = [0, 0]
+        while True:
+            yield from wait(cta.acc_full[buf], aph[buf])
+            tag = cta.acc_unit[buf]
+            if tag == "end":
+                return
+            assert cta.acc[buf] == tag, "epilogue read an incomplete accumulator"
+            cta.seen.append(tag)
+            cta.acc[buf] = None
+            cta.acc_empty[buf].arrive(EPI)
+            if pair and r == 1:
+                ctas[0].acc_empty[buf].arrive(EPI)
+            aph[buf] ^= 1
+            buf ^= 1
+
+    def run_engine(op):
+        if op[0] == "mma":
+            _, st, ab, want, buf, gi = op
+            for c in ctas:
+                assert c.stage[st] == want, "MMA read a stale stage"
+                assert c.abuf[ab] == want, "MMA read a stale A buffer"
+                prev = c.acc[buf]
+                c.acc[buf] = (want[0], gi)
+                assert prev in (None, (want[0], gi)), "accumulator overwritten before it was read"
+        else:
+            for b in op[1]:
+                b.arrive()
+
+    actors = []
+    for r in range(len(ctas)):
+        actors += [producer(r), converter(r, 0), converter(r, 1), epilogue(r)]
+    actors.append(mma())
+    alive = list(actors)
+    idle = 0
+    while alive or copies or engine:
+        kinds = ["actor"] * len(alive) + (["copy"] if copies else []) + (["engine"] if engine else [])
+        k = rng.randrange(len(kinds))
+        if kinds[k] == "copy":
+            cta, st, tag = copies.pop(rng.randrange(len(copies)))
+            cta.stage[st] = tag
+            cta.full[st].complete_tx(1)
+            idle = 0
+        elif kinds[k] == "engine":
+            run_engine(engine.pop(0))
+            idle = 0
+        else:
+            a = alive[k]
+            try:
+                if next(a) == "blocked":
+                    idle += 1
+                else:
+                    idle = 0
+            except StopIteration:
+                alive.remove(a)
+                idle = 0
+        if not copies and not engine and alive and idle > 200 * len(alive):
+            raise AssertionError("deadlock: %d actors blocked with nothing in flight" % len(alive))
+    for c in ctas:
+        want = [(u, gi) for u in range(n_units) for gi in range(kgroups)] if not pair else None
+        if want is not None:
+            assert sorted(c.seen) == want
+    if pair:
+        per = [(u, gi) for u in range(n_units) for gi in range(kgroups)]
+        assert sorted(ctas[0].seen) == per and sorted(ctas[1].seen) == per
+    return True
+
+
+@pytest.mark.parametrize("pair,ns", [(False, 4), (True, 6), (True, 4), (False, 6), (True, 8)])
+@pytest.mark.parametrize("n_units,kch", [(0, 3), (1, 3), (5, 3), (3, 16), (7, 9)])
+def test_protocol_random_interleavings(pair, ns, n_units, kch):
+    for seed in range(30):
+        run_model(pair, ns, n_units, kch, 8, seed)
+
+
+def test_sentinel_without_buffer_wait_is_caught():
+    """Sensitivity: letting the sentinel skip its A-buffer wait (the mistake a
+    GPU parity run exposed as an expired bounded wait) breaks the pair form
+    with more stages than A buffers."""
+    bad = 0
+    for seed in range(60):
+        try:
+            run_model(True, 6, 1, 3, 8, seed, skip_aempty=True)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_odd_stage_count_is_caught(pair):
+    """Sensitivity: with an odd number of stages, k-chunk i - NS belongs to the
+    other converter set, so a set can reach chunk i before the stage's
+    previous copy has landed and pass its parity wait on the earlier phase
+    (why the kernel requires an even count)."""
+    bad = 0
+    for seed in range(40):
+        try:
+            run_model(pair, 5, 5, 3, 8, seed)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
