@@ -254,13 +254,27 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_src_hash(path_id):
-    f = {1: "rowsel_cc.cu", 2: "rowsel_imma.cu", 4: "rowsel_tc.cu"}[path_id]
+# kernel name -> (path id, source file, exact digit products per modular MAC)
+KERNELS = {"rowsel_cc": (1, "rowsel_cc.cu", 1), "rowsel_imma": (2, "rowsel_imma.cu", 16),
+           "tc_gemm": (4, "rowsel_tc.cu", 16), "tc_ingest": (4, "rowsel_tc.cu", 16),
+           "tc_fused": (4, "rowsel_tc.cu", 16), "tc_cluster": (4, "rowsel_tc.cu", 16),
+           "tc_tmem": (4, "rowsel_tmem.cu", 12), "tc_tmem_pair": (4, "rowsel_tmem.cu", 12)}
+# tensor-core path variants that run the tensor-memory kernel (the variant
+# table in rowsel_tc.cu): 12 digit products per modular MAC, the others 16
+TMEM_VARIANT_IDS = (8, 9, 10, 11)
+
+
+def path_products(path, variant):
+    return 12 if path == 4 and variant in TMEM_VARIANT_IDS else 16
+
+
+def kernel_src_hash(kernel):
+    f = KERNELS[kernel][1]
     with open(os.path.join(ROOT, "paper_2604_04696_gb300", "csrc", f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload, batch, path_id):
+def recorded_traffic(kernel, workload, batch):
     """DRAM bytes per launch from a committed ncu capture, or None when absent or
     when the kernel source changed since it was taken."""
     try:
@@ -269,7 +283,7 @@ def recorded_traffic(kernel, workload, batch, path_id):
     except Exception:
         return None
     e = t.get("%s/%s/B%d" % (kernel, workload, batch))
-    if not e or e.get("src_sha") != kernel_src_hash(path_id):
+    if not e or e.get("src_sha") != kernel_src_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -280,35 +294,39 @@ def kernel_roofline(name, w, ms, peaks, workload):
     alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     s = ms / 1e3
-    path_id = {"rowsel_cc": 1, "rowsel_imma": 2, "tc_gemm": 4, "tc_ingest": 4, "tc_fused": 4, "tc_cluster": 4}[name]
-    traffic = recorded_traffic(name, workload, w["B"], path_id)
+    path_id, _, products = KERNELS[name]
+    traffic = recorded_traffic(name, workload, w["B"])
     if name == "tc_ingest":
         b = sizes.query_ct_bytes(w["B"], w["D0"], w["N"], w["L"])
         a = b / s / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": a / peaks["hbm_gbs"], "traffic": traffic,
                 "note": "selection-ciphertext bytes (read once) per launch vs %s copy BW" % peaks["source"]}
-    r = roofline(path_id, w, ms, peaks, workload)
+    r = roofline(path_id, w, ms, peaks, workload, products)
     r["kernel"] = name
     r["traffic"] = traffic
     return r
 
 
-def roofline(path_id, w, ms, peaks, workload):
+def roofline(path_id, w, ms, peaks, workload, products=16):
+    """Roofline of a RowSel step on one path. `products` is the number of exact
+    fp16 digit products the tensor-core kernel spends per modular MAC (16 for
+    the base-256 kernels, 12 for the tensor-memory kernel's 4 x 3 centred
+    digits)."""
     alg = sizes.rowsel_algorithmic_bytes(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     macs = sizes.rowsel_modmacs(w["B"], w["D0"], w["D1"], w["N"], w["L"])
     s = ms / 1e3
     t_hbm = alg / (peaks["hbm_gbs"] * 1e9)
     traffic = None
     if path_id == 4:
-        flops = 2.0 * 16 * macs       # 16 exact fp16 digit products per modular MAC
+        flops = 2.0 * products * macs     # exact fp16 digit products per modular MAC
         t_c = flops / (peaks["bf16_tflops"] * 1e12)
         if t_c >= t_hbm:
             a = flops / s / 1e12
             return {"bound": "tensor", "achieved": a, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": a / peaks["bf16_tflops"], "traffic": traffic,
-                    "note": "fp16 digit-product flops (16 per modular MAC) vs %s cuBLAS bf16 burst "
-                            "(fp16 and bf16 share one nominal dense rate)" % peaks["source"]}
+                    "note": "fp16 digit-product flops (%d per modular MAC) vs %s cuBLAS bf16 burst "
+                            "(fp16 and bf16 share one nominal dense rate)" % (products, peaks["source"])}
     elif path_id == 2:
         ops = 2.0 * 16 * macs         # 16 u8 x u8 products per modular MAC
         imma_peak = 151.0             # TOPS, measured mma.sync m16n8k32 u8 on this GB300 pool
@@ -838,7 +856,7 @@ def main():
         # that one launch, else from its traced per-launch time
         "roofline": kernel_roofline(dom, w_rank, ms if (len(kcount) == 1 and kcount[dom] == 1) else ktimes[dom],
                                     peaks, args.workload),
-        "step_roofline": roofline(path, w_rank, ms, peaks, args.workload),
+        "step_roofline": roofline(path, w_rank, ms, peaks, args.workload, KERNELS[dom][2]),
         "kernels": {k: {"ms": v, "launches_per_step": kcount[k], "share": v * kcount[k] / sum(
             ktimes[x] * kcount[x] for x in ktimes)} for k, v in ktimes.items()},
         "e2e": {"value": e2e_val, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -853,14 +871,31 @@ def main():
         if True:
             sweep = []
             for b in (1, 8, 32, 128, 256):
+                # per batch: autotuned path and tile, captured once into a CUDA
+                # graph (gpir_graph_create), timed as graph replays
                 ws = workload_shape("c3_sweep", b)
                 wk = GpuWorkload(g, torch, ws, mask)
                 g.gpir_autotune(wk.h, b, wk.ct, wk.out, 0, wk.stream)     # fastest path and tile for b
                 chosen = g.gpir_selected_path(wk.h, b)
-                mss, _ = wk.time_steps(0, 10, 3)
-                sweep.append({"batch": b, "path": PATH_NAMES.get(chosen, str(chosen)), "ms": mss,
-                              "queries_s": b / (mss / 1e3),
-                              "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep")["frac"]})
+                gs = torch.cuda.Stream()
+                graph = g.gpir_graph_create([(wk.h, b, wk.ct, wk.out)], chosen, gs)
+                for _ in range(3):
+                    g.gpir_graph_launch(graph, gs)
+                gs.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(gs)
+                for _ in range(10):
+                    g.gpir_graph_launch(graph, gs)
+                e1.record(gs)
+                gs.synchronize()
+                g.gpir_sync(gs, 60000)
+                mss = e0.elapsed_time(e1) / 10
+                g.gpir_graph_destroy(graph)
+                vb = g.gpir_selected_variant(wk.h, b, chosen)
+                sweep.append({"batch": b, "path": PATH_NAMES.get(chosen, str(chosen)), "variant": vb, "ms": mss,
+                              "queries_s": b / (mss / 1e3), "timed": "CUDA-graph replays",
+                              "roofline_frac": roofline(chosen, ws, mss, peaks, "c3_sweep",
+                                                        path_products(chosen, vb))["frac"]})
                 wk.close()
             line["sweep"] = sweep
         line["pir_pipeline"] = run_pir_pipeline(g, torch)

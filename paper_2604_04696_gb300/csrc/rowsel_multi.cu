@@ -2,9 +2,10 @@
 // databases of uneven D0 / D1, Sec. 5.1.1's batched GEMMs generalised to a
 // job list), and CUDA-graph plans of such calls.
 //
-// Tensor-core path: all jobs' work units are numbered into one index space
-// and processed by ONE persistent GEMM launch (after one ingest launch), up
-// to 8 jobs per launch. CUDA-core and IMMA paths: one launch per job.
+// Tensor-core path: one job runs the kernel tuned for its batch; several jobs
+// have their work units numbered into one index space and processed by ONE
+// persistent GEMM launch (after one ingest launch), up to 8 jobs per launch.
+// CUDA-core and IMMA paths: one launch per job.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -24,6 +25,11 @@ int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaSt
   }
   for (uint32_t k = 0; k < njobs; ++k)
     if (!(jobs[k].db->path_mask & p)) return GPIR_ENOTSUP;
+  // one job (a single database's batch, and every graph of one): the kernel
+  // tuned for that batch; several: all of them in one persistent launch pair
+  if (p == GPIR_PATH_TC && njobs == 1)
+    return dispatch(jobs[0].db, jobs[0].batch, jobs[0].ct, jobs[0].out, p, pick_variant(jobs[0].db, jobs[0].batch, p),
+                    stream);
   if (p == GPIR_PATH_TC) return rowsel_tc_multi(jobs, njobs, stream);
   for (uint32_t k = 0; k < njobs; ++k) {
     int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, p,

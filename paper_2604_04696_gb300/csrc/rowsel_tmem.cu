@@ -136,6 +136,7 @@ enum TmemCounter {
   kTCStore,           // converter: tensor-memory store, its wait and the signal
   kTMWaitA,           // MMA: A buffer not converted
   kTMWaitAcc,         // MMA: accumulator not drained
+  kTMIssue,           // MMA: issuing a k-chunk's MMAs and commits
   kTEWaitAcc,         // epilogue: MMAs of the group not done
   kTEBusy,            // epilogue: draining and reducing
   kTIWaitSlot,        // ingest: ring entry not released, or lookahead
@@ -654,6 +655,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
             if (!first && !(ok = TM_TIMED(kTMWaitA, wait(&afull[ab], abph, kErrTmaWait)))) break;
             first = false;
             tc_fence_after();
+            const uint64_t tiss = PROF ? clock64() : 0;
             const uint32_t sb = smem_u32(smem + st * Cfg::STAGE);
             const uint32_t ta = tmem_base + T_A_COL0 + ab * 32u;
 #pragma unroll
@@ -671,6 +673,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
               mma_commit(&empty[st]);
               mma_commit(&aempty[ab]);
             }
+            if (PROF) pc[PROF ? kTMIssue : 0] += clock64() - tiss;
             if (++st == NS) {
               st = 0;
               ph ^= 1u;

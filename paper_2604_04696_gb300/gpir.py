@@ -300,7 +300,7 @@ FUSED_COUNTERS = ["producer_wait_ready", "producer_wait_empty", "mma_wait_full",
                   "ingest_busy", "ingest_wait_slabs", "ingest_push", "cta_cycles"]
 
 
-TMEM_COUNTERS = ["p_wait_ready", "p_wait_empty", "c_wait_full", "c_busy", "c_store", "m_wait_a", "m_wait_acc",
+TMEM_COUNTERS = ["p_wait_ready", "p_wait_empty", "c_wait_full", "c_busy", "c_store", "m_wait_a", "m_wait_acc", "m_issue",
                  "e_wait_acc", "e_busy", "i_wait_slot", "i_wait_box", "i_busy", "i_fence", "cta_cycles"]
 
 
