@@ -26,23 +26,28 @@
 // tiles in the shared-memory image the MMA reads: [slot][n-block][k-chunk] x
 // (192 rows x 64 k) fp16, K-major, 128-byte swizzle, rows v*64 + n (24 KB).
 // Per batch, in one persistent launch (one CTA per SM, or per SM pair):
-//   - ingest warps TMA-load raw p-major boxes (8 slots x 32 rows x 64 k),
-//     encode every residue once into its 4 digit fields (one byte each) and
-//     store slot-major 8 KB tiles [32 rows][64 k] into a ring in global memory
-//     (4 bytes per residue, half the digit bytes), counted in ready[E % R];
+//   - ingest warps TMA-load raw p-major boxes (8 slots x 64 k x the rows of
+//     one m-block), encode every residue once into its 4 digit fields (one
+//     byte each), transpose them into digit planes and store slot-major 8 KB
+//     tiles [32 rows][64 k] into a ring in global memory (4 bytes per
+//     residue, half the digit bytes), counted in ready[E % R];
 //   - the producer bulk-copies, per k-chunk of a unit, the ring tile (8 KB)
 //     and the database tile (24 KB, or its 12 KB half in the SM-pair form) into
 //     a shared-memory stage;
-//   - converter warps turn the ring tile into fp16 digits in registers (one
-//     PRMT, LOP3 and HADD2 per pair of digits) and store them straight into a
-//     tensor-memory A buffer (tcgen05.st): no digit tile in shared memory, and
-//     the MMA reads only B from shared memory;
+//   - converter warps read their digit's plane of the ring tile (a quarter
+//     of the row), turn it into fp16 digits in registers (one PRMT and one
+//     HADD2 per pair of digits) and store them straight into a tensor-memory
+//     A buffer (tcgen05.st): no digit tile in shared memory, and the MMA reads
+//     only B from shared memory;
 //   - one thread issues tcgen05.mma .kind::f16 with A in tensor memory
 //     (M = 128 or 256, N = 192, K = 16);
 //   - epilogue warps drain the double-buffered accumulators and a store warp
 //     writes the p-major output.
-// Tensor memory (512 columns): accumulators at [0, 192) and [192, 384), four
-// A buffers of 32 columns (64 k of fp16 pairs) at 384 + 32 st.
+// Tensor memory (512 columns): accumulators at [0, 192) and [192, 384), and
+// 128 columns of A buffers at 384: four buffers of one k-chunk (64 k of fp16
+// pairs, 32 columns) or two of two consecutive k-chunks (64 columns, one
+// k-chunk from each converter set), per form. The MMA thread waits for a
+// buffer once and issues its MMAs back to back.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -65,7 +70,7 @@ constexpr int T_KGROUP = 8;                          // k-chunks per exact group
 constexpr int T_FLUSH = 4;                           // groups summed before one reduction
 constexpr int T_RAW_TILE = T_MROWS * T_KCHUNK * 4;   // 8 KB ring tile
 constexpr int T_B_TILE = T_NDIG * T_KCHUNK * 2;      // 24 KB
-constexpr int T_ABUF = 4;                           // tensor-memory A buffers (32 columns each)
+constexpr int T_ABUF_MAX = 4;                        // A buffer barriers reserved
 constexpr uint32_t T_PREF = 8;                       // L2 prefetch distance, in k-chunks
 constexpr uint32_t T_ACC_COLS = T_NDIG;
 constexpr uint32_t T_A_COL0 = 2 * T_ACC_COLS;        // 384
@@ -74,26 +79,34 @@ constexpr uint32_t kOffA = 64u * (1u + (1u << 7) + (1u << 14) + (1u << 21));
 constexpr int32_t kOffB = 512 * (1 + (1 << 10));
 
 // Warp roles (896 threads). Tensor-memory lane quarter of a warp = warp % 4.
-constexpr int W_PROD = 0, W_MMA = 1, W_STORE = 2;    // warp 3 idles
+constexpr int W_PROD = 0, W_MMA = 1, W_STORE = 2;
+constexpr int W_RELAY = 3;                           // SM pair: hands finished groups to the odd CTA
 constexpr int W_CONV0 = 4, N_CONV = 8;               // two converter sets of 4 warps (quarters 0..3),
                                                      // set s converts stages s and s + 2
 constexpr int W_EPI0 = 12, N_EPI = 8;                // 8 epilogue warps: quarter, column half
 constexpr int W_ING0 = 20, N_ING = 8;                // 8 ingest warps
 constexpr int T_THREADS = 32 * (W_ING0 + N_ING);     // 896
 static_assert(W_CONV0 % 4 == 0 && W_EPI0 % 4 == 0, "tensor-memory roles start on a lane quarter 0 warp");
-constexpr int T_RAW_BOX = 16 * T_KCHUNK * 2 * 8 * 4; // 64 KB: 16 clients x 64 k x 2 x 8 slots
+constexpr int T_TASK_CLIENTS = T_MROWS / 2;         // clients of one ingest task (one m-block)
 constexpr int T_OUT_BYTES = T_MROWS * T_NCOLS * 4;   // 8 KB
 
-// Shared-memory stages (B tile part + ring tile) are decoupled from the four
-// tensor-memory A buffers: k-chunk i of a CTA uses stage i % NS and A buffer
-// i % T_ABUF, so the SM-pair form, whose stages are smaller, runs a deeper
-// copy pipeline.
+// Shared-memory stages (B tile part + ring tile) are decoupled from the
+// tensor-memory A buffers: k-chunk i of a CTA uses stage i % NS and part
+// i % KPB of A buffer (i / KPB) % NBUF. The ingest loads its task's 64 KB of
+// raw residues as 16 / BOX_CLIENTS boxes into one box buffer, so a smaller box
+// leaves room for more stages.
 template <bool PAIR>
 struct TmemCfg {
   static constexpr int B_BYTES = PAIR ? T_B_TILE / 2 : T_B_TILE;   // this CTA's part of B
   static constexpr int STAGE = T_RAW_TILE + B_BYTES;
-  static constexpr int NS = PAIR ? 6 : 4;
-  static constexpr size_t SMEM = 1024 + (size_t)NS * STAGE + T_RAW_BOX + T_OUT_BYTES + 768;
+  static constexpr int KPB = PAIR ? 2 : 1;                          // k-chunks per A buffer
+  static constexpr int NBUF = 4 / KPB;                              // A buffers (128 columns)
+  static constexpr int BOX_CLIENTS = PAIR ? 8 : 16;                 // clients per ingest box
+  static constexpr int RAW_BOX = BOX_CLIENTS * T_KCHUNK * 2 * 8 * 4;   // x 64 k x 2 x 8 slots x 4 B
+  static constexpr int NS = PAIR ? 8 : 4;
+  static constexpr size_t SMEM = 1024 + (size_t)NS * STAGE + RAW_BOX + T_OUT_BYTES + 1024;
+  static_assert(KPB == 1 || KPB == 2, "an A buffer holds one k-chunk or one of each converter set");
+  static_assert(T_TASK_CLIENTS % BOX_CLIENTS == 0 && BOX_CLIENTS % 4 == 0, "whole boxes per ingest task");
   // Even: a converter set waits full[stage] for k-chunks i, i + 2, ...; the
   // stage's previous k-chunk i - NS must then be one the same set has already
   // waited for, else a parity wait could pass on the phase before it.
@@ -121,7 +134,7 @@ struct TmemParams {
   unsigned long long *ctr;              // [0] next unit, [1] next ingest task
   unsigned int *err;
   unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
-  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, 16 clients)
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, BOX_CLIENTS clients)
   TmLimb limb[GPIR_MAX_LIMBS];
 };
 
@@ -137,6 +150,7 @@ enum TmemCounter {
   kTMWaitA,           // MMA: A buffer not converted
   kTMWaitAcc,         // MMA: accumulator not drained
   kTMIssue,           // MMA: issuing a k-chunk's MMAs and commits
+  kTMHandoff,         // MMA: handing a finished group to the epilogues (tag, commit, arrives)
   kTEWaitAcc,         // epilogue: MMAs of the group not done
   kTEBusy,            // epilogue: draining and reducing
   kTIWaitSlot,        // ingest: ring entry not released, or lookahead
@@ -206,19 +220,37 @@ __device__ __forceinline__ void tmem_ld4x3(uint32_t t0, uint32_t t1, uint32_t t2
 // byte 3 holds y >> 21 <= 128 whole).
 __device__ __forceinline__ uint32_t ct_fields(uint32_t x, uint32_t q, uint32_t h) {
   const uint32_t y = x + kOffA - (x > h ? q : 0u);
-  uint32_t z = (y & 0x7Fu) | ((y << 1) & 0xFFFFFF80u);
-  z = (z & 0x7FFFu) | ((y << 2) & 0xFFFF8000u);
-  z = (z & 0x7FFFFFu) | ((y << 3) & 0xFF800000u);
+  // byte u = field u of y with bit 7 clear (u < 3), byte 3 = y >> 21
+  uint32_t z = (y & 0x7Fu) | ((y << 1) & 0xFFFFFF00u);
+  z = (z & 0x7FFFu) | ((y << 2) & 0xFFFF0000u);
+  z = (z & 0x7FFFFFu) | ((y << 3) & 0xFF000000u);
   return z;
 }
 
-// fp16 pair (digit u of z0, digit u of z1): byte u of each under 0x6400
-// (= 1024 + field exactly), then field - 64 by one HADD2.
-// sel = u | u << 4 | (u + 4) << 8 | (u + 4) << 12 picks byte u of z0 and of z1;
-// mask keeps 7 bits (8 for the top digit u = 3). Both are per-thread values,
-// so a warp whose lanes hold different digits runs one instruction stream.
-__device__ __forceinline__ uint32_t digit_pair(uint32_t z0, uint32_t z1, uint32_t sel, uint32_t mask) {
-  const uint32_t t = (__byte_perm(z0, z1, sel) & mask) | 0x64006400u;
+// Ring tile row (256 bytes, one ciphertext row of a k-chunk): 16-byte chunk
+// c16 = 2 j + h holds, for k octet j, the bytes of digits 2h and 2h + 1 of its
+// 8 residues in k order ([digit 2h: 8 bytes][digit 2h + 1: 8 bytes]), stored
+// at position c16 ^ (row % 8). Byte u of a ring word z is field u of y
+// (bit 7 clear for u < 3), so a digit plane holds the fields as they are.
+
+// Four ring words (k0..k3 in the order the selectors give) -> their four digit
+// planes p[u] = (byte u of k0, k1, k2, k3). sa / sb pick bytes 0, 1 / 2, 3 of
+// a word pair: 0x5140 / 0x7362 in order, 0x1504 / 0x3726 with the pair
+// swapped.
+__device__ __forceinline__ void digit_planes(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, uint32_t sa,
+                                             uint32_t sb, uint32_t p[4]) {
+  const uint32_t t0 = __byte_perm(w0, w1, sa), t1 = __byte_perm(w0, w1, sb);
+  const uint32_t t2 = __byte_perm(w2, w3, sa), t3 = __byte_perm(w2, w3, sb);
+  p[0] = __byte_perm(t0, t2, 0x5410);
+  p[1] = __byte_perm(t0, t2, 0x7632);
+  p[2] = __byte_perm(t1, t3, 0x5410);
+  p[3] = __byte_perm(t1, t3, 0x7632);
+}
+
+// fp16 pair of the fields in bytes 2s and 2s + 1 of plane word w: each byte
+// under 0x6400 (= 1024 + field exactly), then field - 64 by one HADD2.
+__device__ __forceinline__ uint32_t plane_pair(uint32_t w, uint32_t sel) {
+  const uint32_t t = __byte_perm(w, 0x64646464u, sel);   // 0x5140: bytes 0, 1; 0x5342: bytes 2, 3
   const __half2 h = __hadd2(*reinterpret_cast<const __half2 *>(&t),
                             __half2half2(__ushort_as_half((unsigned short)0xE440)));   // -1088
   return *reinterpret_cast<const uint32_t *>(&h);
@@ -297,12 +329,12 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   // stage st: B part at smem + st * STAGE (1024-aligned), ring tile after it
   constexpr int NS = Cfg::NS;
   uint8_t *rawbox = smem + NS * Cfg::STAGE;
-  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + T_RAW_BOX);
-  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + T_RAW_BOX + T_OUT_BYTES);
+  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + Cfg::RAW_BOX);
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + Cfg::RAW_BOX + T_OUT_BYTES);
   uint64_t *empty = full + NS;
-  uint64_t *afull = empty + NS;                   // [T_ABUF] A buffer converted (pair: both CTAs')
-  uint64_t *aempty = afull + T_ABUF;              // [T_ABUF] A buffer read by its MMAs
-  uint64_t *acc_full = aempty + T_ABUF;
+  uint64_t *afull = empty + NS;                   // [NBUF] A buffer converted (pair: both CTAs')
+  uint64_t *aempty = afull + T_ABUF_MAX;          // [NBUF] A buffer read by its MMAs
+  uint64_t *acc_full = aempty + T_ABUF_MAX;
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *box_bar = acc_empty + 2;
   uint64_t *ostage_full = box_bar + 1;
@@ -315,7 +347,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   uint64_t *mail = ostage_unit + 1;               // pair: [4] claimed units, even -> odd CTA
   uint64_t *mail_full = mail + 4;
   uint64_t *mail_empty = mail_full + 4;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mail_empty + 4);
+  uint64_t *hand_full = mail_empty + 4;           // pair (even CTA): [2] group handed to the relay
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hand_full + 2);
   volatile uint32_t *abort_flag = tmem_slot + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -325,9 +358,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       mbar_init(&full[s2], 1);
       mbar_init(&empty[s2], 1);
     }
-    for (int a = 0; a < T_ABUF; ++a) {
-      // single CTA: the 4 converter warps of a set; pair (even CTA): both CTAs' warps
-      mbar_init(&afull[a], (PAIR && rank == 0) ? 8 : 4);
+    for (int a = 0; a < Cfg::NBUF; ++a) {
+      // the 4 warps of each converter set filling the buffer (KPB sets); in
+      // the pair, the even CTA counts both CTAs' warps
+      mbar_init(&afull[a], 4 * Cfg::KPB * ((PAIR && rank == 0) ? 2 : 1));
       mbar_init(&aempty[a], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -338,6 +372,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       mbar_init(&mail_full[i], 1);
       mbar_init(&mail_empty[i], 1);
     }
+    for (int b = 0; b < 2; ++b) mbar_init(&hand_full[b], 1);
     mbar_init(box_bar, 1);
     mbar_init(ostage_full, N_EPI);
     mbar_init(ostage_empty, 1);
@@ -551,19 +586,19 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     // ---------------- converters: ring tile (smem) -> fp16 digits -> tensor memory ----------------
     // Thread = tensor-memory lane (row m_hi*32 + u*8 + m_lo of the A operand):
     // ciphertext row m = m_hi*8 + m_lo of the m-block, digit u. Set cs
-    // converts stages cs, cs + 2, cs, ... (two sets hide each other's latency).
+    // converts k-chunks i = cs, cs + 2, ... (two sets hide each other's
+    // latency) into part i % KPB of A buffer (i / KPB) % NBUF.
     const uint32_t qw = (uint32_t)(warp & 3);
     const uint32_t cs = (uint32_t)(warp - W_CONV0) >> 2;
     const int u = lane >> 3, m_lo = lane & 7;
     const int m = (int)qw * 8 + m_lo;
     const uint32_t lane_base = tmem_base + ((qw * 32u) << 16);
-    const uint32_t dsel = (uint32_t)(u | (u << 4) | ((u + 4) << 8) | ((u + 4) << 12));
-    const uint32_t dmask = u < 3 ? 0x007F007Fu : 0x00FF00FFu;
     const bool conv_counter = PROF && warp == W_CONV0 && lane == 0;
     for (uint32_t it = 0;; ++it) {
       const uint32_t i = 2u * it + cs;                      // this CTA's k-chunk sequence number
       const uint32_t st = i % NS, ph = (i / NS) & 1u;
-      const uint32_t ab = i % T_ABUF, aph = (i / T_ABUF) & 1u;
+      const uint32_t bi = i / Cfg::KPB, ab = bi % Cfg::NBUF, aph = (bi / Cfg::NBUF) & 1u;
+      const uint32_t acol = T_A_COL0 + ab * (32u * Cfg::KPB) + (i % Cfg::KPB) * 32u;
       const bool okf = conv_counter ? TM_TIMED(kTCWaitFull, wait(&full[st], ph, kErrTmaWait))
                                     : wait(&full[st], ph, kErrTmaWait);
       if (!__all_sync(0xffffffffu, okf)) break;
@@ -586,18 +621,17 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       }
       // the unit's last ring tile is in shared memory: its ring entry may be reused
       if (qw == 0 && lane == 0 && stage_kc[st] + 1 == p.kch) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
-      const uint4 *row = reinterpret_cast<const uint4 *>(smem + st * Cfg::STAGE + Cfg::B_BYTES) + m * 16;
+      // this thread's digit plane: 8 bytes per k octet (conflict-free: the
+      // warp's 32 reads of a step cover every bank twice)
+      const uint2 *row = reinterpret_cast<const uint2 *>(smem + st * Cfg::STAGE + Cfg::B_BYTES) + m * 32;
       uint32_t wv[32];
 #pragma unroll
-      for (int c16 = 0; c16 < 16; ++c16) {
-        const uint4 z = row[c16 ^ (m & 7)];
-        if ((c16 >> 1) & 1) {   // odd k octet: the ring holds its k offsets pairwise swapped
-          wv[2 * c16] = digit_pair(z.y, z.x, dsel, dmask);
-          wv[2 * c16 + 1] = digit_pair(z.w, z.z, dsel, dmask);
-        } else {
-          wv[2 * c16] = digit_pair(z.x, z.y, dsel, dmask);
-          wv[2 * c16 + 1] = digit_pair(z.z, z.w, dsel, dmask);
-        }
+      for (int j = 0; j < 8; ++j) {
+        const uint2 z = row[(((2 * j + (u >> 1)) ^ (m & 7)) << 1) | (u & 1)];
+        wv[4 * j] = plane_pair(z.x, 0x5140u);
+        wv[4 * j + 1] = plane_pair(z.x, 0x5342u);
+        wv[4 * j + 2] = plane_pair(z.y, 0x5140u);
+        wv[4 * j + 3] = plane_pair(z.y, 0x5342u);
       }
       const uint64_t tst = PROF ? clock64() : 0;
       if (conv_counter) pc[PROF ? kTCBusy : 0] += tst - tconv;
@@ -605,7 +639,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       // been read by its MMAs before they overwrite it
       if (!__all_sync(0xffffffffu, wait(&aempty[ab], aph ^ 1u, kErrMmaWait))) break;
       tc_fence_after();
-      tmem_st32(lane_base + T_A_COL0 + ab * 32u, wv);
+      tmem_st32(lane_base + acol, wv);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
       __syncwarp();
@@ -620,26 +654,31 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   } else if (warp == W_MMA) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      uint32_t st = 0, ph = 0, buf = 0, ab = 0, abph = 0;
+      // k-chunk i of this CTA sits in part i % KPB of A buffer (i / KPB) %
+      // NBUF; the MMA thread waits for a buffer at its first part (all parts
+      // are converted by then: the count spans their sets) and commits it
+      // after the last
+      uint32_t st = 0, ph = 0, buf = 0, i = 0;
       uint32_t aph[2] = {0, 0};
       bool ok = true;
       const uint32_t kgroups = (p.kch + T_KGROUP - 1) / T_KGROUP;
+      auto wait_a = [&]() -> bool {
+        if (i % Cfg::KPB) return true;
+        const uint32_t bi = i / Cfg::KPB;
+        return TM_TIMED(kTMWaitA, wait(&afull[bi % Cfg::NBUF], (bi / Cfg::NBUF) & 1u, kErrTmaWait));
+      };
       for (;;) {
         if (PAIR && rank != 0) {
           // odd CTA: its converters signal the even CTA directly; nothing to issue
           break;
         }
-        if (!(ok = TM_TIMED(kTMWaitA, wait(&afull[ab], abph, kErrTmaWait)))) break;
+        if (!(ok = wait_a())) break;
         const uint64_t u = stage_unit[st];
         if (u == kNoUnit) {
           if ((ok = wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait))) {
             acc_unit[buf] = kNoUnit;
-            if constexpr (PAIR) {
-              // the odd CTA's epilogue learns the end of work from its own acc_unit
-              st_cluster_u64(map_peer(smem_u32(&acc_unit[buf]), 1), kNoUnit);
-              mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
-              mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
-            }
+            // pair: the relay tells the odd CTA's epilogue (its own acc_unit)
+            if constexpr (PAIR) mbar_arrive(&hand_full[buf]);
             mbar_arrive_cnt(&acc_full[buf], 2);
           }
           break;
@@ -652,12 +691,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           const uint32_t c0 = gi * T_KGROUP;
           const uint32_t c1 = min(p.kch, c0 + T_KGROUP);
           for (uint32_t kc = c0; kc < c1; ++kc) {
-            if (!first && !(ok = TM_TIMED(kTMWaitA, wait(&afull[ab], abph, kErrTmaWait)))) break;
+            if (!first && !(ok = wait_a())) break;
             first = false;
             tc_fence_after();
             const uint64_t tiss = PROF ? clock64() : 0;
             const uint32_t sb = smem_u32(smem + st * Cfg::STAGE);
-            const uint32_t ta = tmem_base + T_A_COL0 + ab * 32u;
+            const uint32_t ab = (i / Cfg::KPB) % Cfg::NBUF;
+            const bool a_done = i % Cfg::KPB == Cfg::KPB - 1;
+            const uint32_t ta = tmem_base + T_A_COL0 + ab * (32u * Cfg::KPB) + (i % Cfg::KPB) * 32u;
 #pragma unroll
             for (int k16 = 0; k16 < T_KCHUNK / 16; ++k16) {
               const uint32_t acc = (kc > c0 || k16 > 0) ? 1u : 0u;
@@ -668,32 +709,33 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
             }
             if constexpr (PAIR) {
               mma_commit_pair(&empty[st]);
-              mma_commit_pair(&aempty[ab]);
+              if (a_done) mma_commit_pair(&aempty[ab]);
             } else {
               mma_commit(&empty[st]);
-              mma_commit(&aempty[ab]);
+              if (a_done) mma_commit(&aempty[ab]);
             }
             if (PROF) pc[PROF ? kTMIssue : 0] += clock64() - tiss;
             if (++st == NS) {
               st = 0;
               ph ^= 1u;
             }
-            if (++ab == T_ABUF) {
-              ab = 0;
-              abph ^= 1u;
-            }
+            ++i;
           }
           if (!ok) break;
+          const uint64_t thand = PROF ? clock64() : 0;
           const uint64_t tag = u | ((gi + 1 == kgroups) ? (1ull << 63) : 0ull);
           acc_unit[buf] = tag;
           if constexpr (PAIR) {
-            st_cluster_u64(map_peer(smem_u32(&acc_unit[buf]), 1), tag);
-            mbar_arrive_remote(map_peer(smem_u32(&acc_full[buf]), 1));
+            // the tag reaches the odd CTA through the relay warp: its
+            // cluster-scope release arrive can wait for the SM's outstanding
+            // ring stores, which must not hold up the next group's MMAs
             mma_commit_pair(&acc_full[buf]);
+            mbar_arrive(&hand_full[buf]);
           } else {
             mma_commit(&acc_full[buf]);
           }
           mbar_arrive(&acc_full[buf]);
+          if (PROF) pc[PROF ? kTMHandoff : 0] += clock64() - thand;
           aph[buf] ^= 1u;
           buf ^= 1u;
         }
@@ -810,6 +852,27 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         for (int i = 0; i < 8; ++i) res[i] = 0;
       }
     }
+  } else if (PAIR && warp == W_RELAY) {
+    // ---------------- relay (pair, even CTA): group tags to the odd CTA ----------------
+    // The odd CTA's acc_full completes on the MMA commit (multicast) and on
+    // this remote arrive, whose release orders the tag store before it. The
+    // MMA thread cannot reuse acc_unit[b] before the odd epilogue, which needs
+    // this arrive, has drained the accumulator.
+    if (rank == 0 && lane == 0) {
+      uint32_t hb = 0, hph[2] = {0, 0};
+      for (;;) {
+        if (!wait(&hand_full[hb], hph[hb], kErrMmaWait)) break;
+        const uint64_t tag = acc_unit[hb];
+        st_cluster_u64(map_peer(smem_u32(&acc_unit[hb]), 1), tag);
+        mbar_arrive_remote(map_peer(smem_u32(&acc_full[hb]), 1));
+        if (tag == kNoUnit) {
+          mbar_arrive_remote(map_peer(smem_u32(&acc_full[hb]), 1));   // no commit comes after the last group
+          break;
+        }
+        hph[hb] ^= 1u;
+        hb ^= 1u;
+      }
+    }
   } else if (warp == W_STORE) {
     // ---------------- output store warp ----------------
     uint32_t ph = 0;
@@ -840,11 +903,12 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     }
   } else if (warp >= W_ING0) {
     // ---------------- ingest (8 warps, 256 threads) ----------------
-    // Task = (entry E, k-chunk kc): one 64 KB TMA box of 8 slots x 32 rows x
-    // 64 k. A thread handles (row, k octet, slot half) items; for each slot it
-    // stores the 8 encoded residues of its row and
-    // octet as two 16-byte chunks of the slot's ring tile, chunk c16 of row m
-    // at position c16 ^ (m % 8) (conflict-free reads by the converters).
+    // Task = (entry E, k-chunk kc): 64 KB of raw residues, 8 slots x 32 rows
+    // x 64 k, loaded as 16 / BOX_CLIENTS TMA boxes of BOX_CLIENTS clients,
+    // one after the other into the box buffer. A thread handles (row, k
+    // octet, slot half) items; for each slot it stores the 8 encoded residues
+    // of its row and octet as their four digit planes in two 16-byte chunks of
+    // the slot's ring tile, chunk c16 of row m at position c16 ^ (m % 8).
     const int it = (warp - W_ING0) * 32 + lane;
     constexpr int NT = 32 * N_ING;
     const uint64_t pol_last = l2_policy_evict_last();
@@ -866,84 +930,92 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       if (it == 0) {
         const bool near = p.lookahead == 0 || E < p.lookahead ||
                           TM_TIMED(kTIWaitSlot, wait_claims(((E - p.lookahead) >> (PAIR ? 1 : 0)) * p.upe));
-        if (near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
-                                                                   (uint32_t)((E / p.R) * p.upe))))) {
-          mbar_arrive_expect_tx(box_bar, T_RAW_BOX);
-          if (p.hints)
-            tma_load_5d_hint(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
-                             (int)(mb * (T_MROWS / 2)), l2_policy_evict_first());
-          else
-            tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK),
-                        (int)(mb * (T_MROWS / 2)));
-          issued = true;
-          *task_slot = c;
-        } else {
-          *task_slot = kNoUnit;
-        }
+        *task_slot = (near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
+                                                                             (uint32_t)((E / p.R) * p.upe)))))
+                         ? c
+                         : kNoUnit;
       }
       asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
       if (*task_slot == kNoUnit) break;
-      uint32_t got = (it == 0 ? TM_TIMED(kTIWaitBox, wait(box_bar, rph, kErrTmaWait))
-                              : wait(box_bar, rph, kErrTmaWait)) ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
-          " selp.u32 %0, 1, 0, pout;\n}"
-          : "=r"(got)
-          : "r"(got), "n"(NT)
-          : "memory");
-      if (!got) break;
-      rph ^= 1u;
-      if (it == 0) issued = false;
       const uint64_t tbusy = PROF ? clock64() : 0;
+      uint64_t twait = 0;
       const uint32_t q = p.limb[l].q, h = p.limb[l].h;
       const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox);
       uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
       // Lane = (k octet j, row parity rp, slot half sh): a warp's 16-byte box
       // reads at step kk cover all 8 bank groups (4 wavefronts per 512 B, the
       // minimum) because the thread reads k offset kk ^ (j & 1) and slot half
-      // sh = s4 ^ ((j >> 1) & 1); it stores position kk of its octet's ring
-      // chunk pair from that read, so ring position p of octet j holds k offset
-      // p ^ (j & 1) (the converter swaps the pair for odd octets).
+      // sh = s4 ^ ((j >> 1) & 1); the byte selectors of the plane transpose
+      // undo the swap of k offsets in odd octets.
       const int j = lane >> 2, rp = (lane >> 1) & 1;
       const int j0 = j & 1, sh = (lane & 1) ^ ((j >> 1) & 1);
+      const uint32_t sel_a = j0 ? 0x1504u : 0x5140u, sel_b = j0 ? 0x3726u : 0x7362u;
+      bool got_all = true;
 #pragma unroll 1
-      for (int cc = it >> 5; cc < 16; cc += NT / 32) {
-        const int m_local = cc * 2 + rp;
-        uint32_t z[8][4];   // [position kk][slot in half]
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-          const uint4 v = raw4[((cc * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh];
-          z[kk][0] = ct_fields(v.x, q, h);
-          z[kk][1] = ct_fields(v.y, q, h);
-          z[kk][2] = ct_fields(v.z, q, h);
-          z[kk][3] = ct_fields(v.w, q, h);
+      for (int part = 0; part < T_TASK_CLIENTS / Cfg::BOX_CLIENTS; ++part) {
+        if (part > 0) asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");   // box buffer read out
+        if (it == 0) {
+          const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
+          mbar_arrive_expect_tx(box_bar, Cfg::RAW_BOX);
+          if (p.hints)
+            tma_load_5d_hint(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0,
+                             l2_policy_evict_first());
+          else
+            tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0);
+          issued = true;
         }
+        const uint64_t tw0 = PROF ? clock64() : 0;
+        uint32_t got = wait(box_bar, rph, kErrTmaWait) ? 1u : 0u;
+        if (PROF && it == 0) twait += clock64() - tw0;
+        asm volatile(
+            "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
+            " selp.u32 %0, 1, 0, pout;\n}"
+            : "=r"(got)
+            : "r"(got), "n"(NT)
+            : "memory");
+        if (!got) {
+          got_all = false;
+          break;
+        }
+        rph ^= 1u;
+        if (it == 0) issued = false;
+#pragma unroll 1
+        for (int cb = it >> 5; cb < Cfg::BOX_CLIENTS; cb += NT / 32) {
+          const int m_local = (part * Cfg::BOX_CLIENTS + cb) * 2 + rp;
+          uint32_t z[8][4];   // [position kk][slot in half]
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int sl = sh * 4 + i;
-          if (t0 + sl >= p.N) continue;
-          uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
-          uint4 lo, hi;
-          lo.x = z[0][i];
-          lo.y = z[1][i];
-          lo.z = z[2][i];
-          lo.w = z[3][i];
-          hi.x = z[4][i];
-          hi.y = z[5][i];
-          hi.z = z[6][i];
-          hi.w = z[7][i];
-          if (p.hints) {
-            st_global_v4_hint(&tile[m_local * 16 + ((2 * j) ^ (m_local & 7))], lo, pol_last);
-            st_global_v4_hint(&tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))], hi, pol_last);
-          } else {
-            tile[m_local * 16 + ((2 * j) ^ (m_local & 7))] = lo;
-            tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))] = hi;
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint4 v = raw4[((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh];
+            z[kk][0] = ct_fields(v.x, q, h);
+            z[kk][1] = ct_fields(v.y, q, h);
+            z[kk][2] = ct_fields(v.z, q, h);
+            z[kk][3] = ct_fields(v.w, q, h);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int sl = sh * 4 + i;
+            if (t0 + sl >= p.N) continue;
+            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
+            uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
+            digit_planes(z[0][i], z[1][i], z[2][i], z[3][i], sel_a, sel_b, pl);
+            digit_planes(z[4][i], z[5][i], z[6][i], z[7][i], sel_a, sel_b, ph);
+            const uint4 lo = make_uint4(pl[0], ph[0], pl[1], ph[1]);   // chunk 2j: digits 0, 1
+            const uint4 hi = make_uint4(pl[2], ph[2], pl[3], ph[3]);   // chunk 2j + 1: digits 2, 3
+            if (p.hints) {
+              st_global_v4_hint(&tile[m_local * 16 + ((2 * j) ^ (m_local & 7))], lo, pol_last);
+              st_global_v4_hint(&tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))], hi, pol_last);
+            } else {
+              tile[m_local * 16 + ((2 * j) ^ (m_local & 7))] = lo;
+              tile[m_local * 16 + ((2 * j + 1) ^ (m_local & 7))] = hi;
+            }
           }
         }
       }
+      if (!got_all) break;
+      if (PROF && it == 0) pc[PROF ? kTIWaitBox : 0] += twait;
       fence_proxy_async_global();
       const uint64_t tfence = PROF ? clock64() : 0;
-      if (PROF && it == 0) pc[PROF ? kTIBusy : 0] += tfence - tbusy;
+      if (PROF && it == 0) pc[PROF ? kTIBusy : 0] += tfence - tbusy - twait;
       asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
       if (it == 0) {
         __threadfence();
@@ -1131,7 +1203,8 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
     const uint64_t dims[5] = {N, L, 2, db->d0, batch};
     const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
                              (uint64_t)db->d0 * 2 * L * N * 4};
-    const uint32_t box[5] = {8, 1, 2, (uint32_t)T_KCHUNK, (uint32_t)(T_MROWS / 2)};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)T_KCHUNK,
+                             (uint32_t)(pair ? TmemCfg<true>::BOX_CLIENTS : TmemCfg<false>::BOX_CLIENTS)};
     rc = encode_tiled_u32(&tp.ct_map, ct, 5, dims, str, box);
     if (rc != GPIR_OK) return rc;
   }

@@ -301,16 +301,16 @@ FUSED_COUNTERS = ["producer_wait_ready", "producer_wait_empty", "mma_wait_full",
 
 
 TMEM_COUNTERS = ["p_wait_ready", "p_wait_empty", "c_wait_full", "c_busy", "c_store", "m_wait_a", "m_wait_acc", "m_issue",
-                 "e_wait_acc", "e_busy", "i_wait_slot", "i_wait_box", "i_busy", "i_fence", "cta_cycles"]
+                 "m_handoff", "e_wait_acc", "e_busy", "i_wait_slot", "i_wait_box", "i_busy", "i_fence", "cta_cycles"]
 
 
 def gpir_trace_counters(names=None):
     """{name: cycles} of the last traced fused, cluster or tensor-memory launch
     (names: FUSED_COUNTERS, the default, or TMEM_COUNTERS)."""
     names = FUSED_COUNTERS if names is None else names
-    buf = (ctypes.c_ulonglong * 16)()
+    buf = (ctypes.c_ulonglong * 32)()
     n = ctypes.c_uint32(0)
-    _check(lib.gpir_trace_counters(buf, 16, ctypes.byref(n)), "gpir_trace_counters")
+    _check(lib.gpir_trace_counters(buf, 32, ctypes.byref(n)), "gpir_trace_counters")
     return {names[i] if i < len(names) else str(i): int(buf[i]) for i in range(n.value)}
 
 

@@ -317,8 +317,8 @@ def test_cuda_core_model_equals_oracle():
 # q and of magnitude below 2^27, so the product mod q is unchanged. Then
 #   - ciphertext residues: y = x~ + O_A, O_A = 64 (1 + 2^7 + 2^14 + 2^21),
 #     carried through the digit ring as z, the four 7-bit fields of y spread
-#     one per byte (byte u = (y >> 7u) & 127, byte 3 = y >> 21 <= 128; bit 7 of
-#     bytes 0..2 is don't-care); digit d_u = field_u - 64 in [-64, 64];
+#     one per byte (byte u = (y >> 7u) & 127 with bit 7 clear, byte 3 =
+#     y >> 21 <= 128); digit d_u = field_u - 64 in [-64, 64];
 #   - database residues: Y = v~ + O_B, O_B = 512 (1 + 2^10), digits
 #     e_0 = (Y & 1023) - 512, e_1 = ((Y >> 10) & 1023) - 512, e_2 = Y >> 20
 #     (arithmetic shift), e_v in [-512, 511] x [-128, 128];
@@ -342,17 +342,16 @@ def ct_fields(x, q):
     x = np.asarray(x, dtype=np.uint32)
     h = np.uint32((q - 1) // 2)
     y = (x + np.uint32(O_A) - np.where(x > h, np.uint32(q), np.uint32(0))).astype(np.uint32)
-    z = (y & np.uint32(0x7F)) | ((y << np.uint32(1)) & np.uint32(0xFFFFFF80))
-    z = (z & np.uint32(0x7FFF)) | ((y << np.uint32(2)) & np.uint32(0xFFFF8000))
-    z = (z & np.uint32(0x7FFFFF)) | ((y << np.uint32(3)) & np.uint32(0xFF800000))
+    z = (y & np.uint32(0x7F)) | ((y << np.uint32(1)) & np.uint32(0xFFFFFF00))
+    z = (z & np.uint32(0x7FFF)) | ((y << np.uint32(2)) & np.uint32(0xFFFF0000))
+    z = (z & np.uint32(0x7FFFFF)) | ((y << np.uint32(3)) & np.uint32(0xFF000000))
     return z
 
 
 def ct_digit_fp16(z, u):
-    """Digit u of ring words z as the kernel builds it: the byte (7 bits, all 8
-    for the top digit) under 0x6400 as an fp16, then one fp16 addition of -1088."""
-    mask = 0x7F if u < 3 else 0xFF
-    bits = ((z >> np.uint32(8 * u)) & np.uint32(mask)).astype(np.uint16) | np.uint16(0x6400)
+    """Digit u of ring words z as the kernel builds it: byte u as it is under
+    0x6400 as an fp16, then one fp16 addition of -1088."""
+    bits = ((z >> np.uint32(8 * u)) & np.uint32(0xFF)).astype(np.uint16) | np.uint16(0x6400)
     return (bits.view(np.float16) + np.float16(-1088.0)).astype(np.float16)
 
 
@@ -414,11 +413,23 @@ def test_ring_encoding_and_fp16_digits_reconstruct_the_centred_residue():
         e = db_digits12(x, q)
         assert e[..., :2].min() >= -512 and e[..., :2].max() <= 511 and np.abs(e[..., 2]).max() <= 128
         assert np.array_equal((e * np.array([1, 1 << 10, 1 << 20])).sum(-1), xt)
-    # every digit and its fp16 image exact: the fp16 arithmetic equals the integer one
+    # every byte and its fp16 image exact: the fp16 arithmetic equals the integer one
     z = np.arange(0, 1 << 16, dtype=np.uint32) * np.uint32(0x01010101 // 257 + 1)
     for u in range(4):
-        f = (z >> np.uint32(8 * u)) & np.uint32(0x7F if u < 3 else 0xFF)
+        f = (z >> np.uint32(8 * u)) & np.uint32(0xFF)
         assert np.array_equal(ct_digit_fp16(z, u).astype(np.int64), f.astype(np.int64) - 64)
+
+
+def test_ring_encoding_clears_bit_7_of_the_low_fields():
+    """The converters take each byte of a ring word as it is, so the encoding
+    must leave bit 7 of bytes 0..2 clear for every residue below q."""
+    rng = np.random.default_rng(19)
+    for q in list(PRIMES) + [17, 268042241]:
+        h = (q - 1) // 2
+        x = np.concatenate([rng.integers(0, q, 20000), [0, h, h + 1, q - 1]]).astype(np.uint32)
+        z = ct_fields(x, q)
+        for u in range(3):
+            assert ((z >> np.uint32(8 * u + 7)) & np.uint32(1)).max() == 0
 
 
 def test_tmem_model_matches_oracle_random():

@@ -11,15 +11,23 @@ count, transaction bytes, phase parity; no code shared with the CUDA source):
     copies land asynchronously), and ends with a sentinel in two consecutive
     stages, one per converter set; the pair's producers then wait for the
     commits of their other stages;
-  - converter set c (two sets of four warps) takes k-chunks i = c, c + 2, ...:
-    waits full[stage], waits aempty[i % NA] (the A buffer's previous k-chunk
-    read by its MMAs; also before a sentinel), stops at a sentinel after
-    arriving on afull, else writes the A buffer and arrives on afull[i % NA]
-    (in the pair, both CTAs' sets arrive on the even CTA's afull, count 8);
-  - the (even CTA's) MMA thread waits afull, issues the k-chunk's MMAs, which
-    read both CTAs' stage and A buffer and accumulate into both CTAs' tensor
-    memory, and commits to empty[stage] and aempty[buffer] (both CTAs in the
-    pair); after each 512-row group it commits to acc_full;
+  - k-chunk i goes into part i % KPB of A buffer (i // KPB) % NBUF (KPB = 1:
+    four buffers of one k-chunk; KPB = 2: two buffers of two); converter set
+    c (two sets of four warps) takes k-chunks i = c, c + 2, ...: it waits
+    full[stage], waits aempty of its buffer (the buffer's previous k-chunks
+    read by their MMAs; also before a sentinel), stops at a sentinel after
+    arriving on afull, else writes its part and arrives on afull (count
+    4 KPB; in the pair, both CTAs' sets arrive on the even CTA's afull, count
+    8 KPB);
+  - the (even CTA's) MMA thread waits afull at the first part of a buffer
+    only, issues each k-chunk's MMAs, which read both CTAs' stage and A
+    buffer part and accumulate into both CTAs' tensor memory, commits to
+    empty[stage] after each k-chunk and to aempty[buffer] after the last
+    part (both CTAs in the pair); after each 512-row group it commits to
+    acc_full (both CTAs) and arrives on its own; in the pair a relay warp of
+    the even CTA then copies the group's tag into the odd CTA and arrives on
+    the odd CTA's acc_full, so that this release arrive does not hold up the
+    MMA thread;
   - the epilogues drain the accumulators (acc_full / acc_empty, double
     buffered); the odd CTA also arrives on the even CTA's acc_empty.
 Checked: no deadlock; every MMA reads, in both CTAs, the stage and A buffer of
@@ -31,7 +39,6 @@ import random
 
 import pytest
 
-NA = 4
 EPI = 8
 
 
@@ -62,27 +69,31 @@ class Bar:
 
 
 class Cta:
-    def __init__(self, ns, afull_count, acc_empty_count):
+    def __init__(self, ns, nbuf, afull_count, acc_empty_count):
         self.full = [Bar(1) for _ in range(ns)]
         self.empty = [Bar(1) for _ in range(ns)]
-        self.afull = [Bar(afull_count) for _ in range(NA)]
-        self.aempty = [Bar(1) for _ in range(NA)]
+        self.afull = [Bar(afull_count) for _ in range(nbuf)]
+        self.aempty = [Bar(1) for _ in range(nbuf)]
         self.acc_full = [Bar(2) for _ in range(2)]
         self.acc_empty = [Bar(acc_empty_count) for _ in range(2)]
+        self.hand_full = [Bar(1) for _ in range(2)]
         self.stage = [None] * ns            # data in the stage: (unit, kc) once landed
         self.stage_unit = [None] * ns
-        self.abuf = [None] * NA             # (unit, kc) converted into A buffer
+        self.abuf = [[None, None] for _ in range(nbuf)]  # (unit, kc) converted into each part
         self.acc_unit = [None] * 2
         self.acc = [None] * 2               # (unit, group) accumulated
         self.seen = []                      # epilogue log
 
 
-def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
+def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, afull_sets=None,
+              relay_early=False):
     rng = random.Random(seed)
+    nbuf = 4 // kpb
+    sets = kpb if afull_sets is None else afull_sets
     if pair:
-        ctas = [Cta(ns, 8, 2 * EPI), Cta(ns, 4, EPI)]
+        ctas = [Cta(ns, nbuf, 8 * sets, 2 * EPI), Cta(ns, nbuf, 4 * sets, EPI)]
     else:
-        ctas = [Cta(ns, 4, EPI)]
+        ctas = [Cta(ns, nbuf, 4 * sets, EPI)]
     mail, mail_full, mail_empty = [None] * 4, [Bar(1) for _ in range(4)], [Bar(1) for _ in range(4)]
     claims = [0]
     copies = []
@@ -151,35 +162,45 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
         while True:
             i = 2 * it + cs
             st, ph = i % ns, (i // ns) & 1
-            ab, aph = i % NA, (i // NA) & 1
+            bi = i // kpb
+            ab, aph, part = bi % nbuf, (bi // nbuf) & 1, i % kpb
             yield from wait(cta.full[st], ph)
             tag = cta.stage_unit[st]
-            # the A buffer's previous k-chunk must have been read by its MMAs,
-            # also before a sentinel: in the pair, an early sentinel arrival
-            # would complete the even CTA's count-8 afull phase of that
-            # previous k-chunk without the other CTA's arrivals
+            # the A buffer's previous pair of k-chunks must have been read by
+            # its MMAs, also before a sentinel: an early sentinel arrival would
+            # complete the afull phase of that previous pair without the other
+            # set's (or, in the pair, the other CTA's) arrivals
             if not (skip_aempty and tag == "end"):
                 yield from wait(cta.aempty[ab], aph ^ 1)
             if tag == "end":
                 target.afull[ab].arrive(4)
                 return
             assert cta.stage[st] == tag, "converter read a stage that has not landed"
-            cta.abuf[ab] = tag
+            cta.abuf[ab][part] = tag
             target.afull[ab].arrive(4)
             it += 1
 
     def mma():
         me = ctas[0]
-        st = ph = buf = ab = abph = 0
+        st = ph = buf = 0
+        ci = [0]                  # k-chunk sequence number
+
+        def wait_a():
+            i = ci[0]
+            if i % kpb == 0:
+                bi = i // kpb
+                yield from wait(me.afull[bi % nbuf], (bi // nbuf) & 1)
+
         aph = [0, 0]
         while True:
-            yield from wait(me.afull[ab], abph)
+            yield from wait_a()
             tag = me.stage_unit[st]
             if tag == "end":
                 yield from wait(me.acc_empty[buf], aph[buf] ^ 1)
-                for c in ctas:
-                    c.acc_unit[buf] = "end"
-                    c.acc_full[buf].arrive(2)
+                me.acc_unit[buf] = "end"
+                if pair:
+                    me.hand_full[buf].arrive()
+                me.acc_full[buf].arrive(2)
                 return
             u = tag[0]
             first = True
@@ -187,19 +208,43 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
                 yield from wait(me.acc_empty[buf], aph[buf] ^ 1)
                 for kc in range(gi * kgroup, min(kch, (gi + 1) * kgroup)):
                     if not first:
-                        yield from wait(me.afull[ab], abph)
+                        yield from wait_a()
                     first = False
-                    engine.append(("mma", st, ab, (u, kc), buf, gi))
-                    engine.append(("commit", [c.empty[st] for c in ctas] + [c.aempty[ab] for c in ctas]))
+                    i = ci[0]
+                    ab, half = (i // kpb) % nbuf, i % kpb
+                    engine.append(("mma", st, (ab, half), (u, kc), buf, gi))
+                    engine.append(("commit", [c.empty[st] for c in ctas]))
+                    if half == kpb - 1:
+                        engine.append(("commit", [c.aempty[ab] for c in ctas]))
                     st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
-                    ab, abph = (ab + 1) % NA, abph ^ (ab + 1 == NA)
-                for c in ctas:
-                    c.acc_unit[buf] = (u, gi)
+                    ci[0] += 1
+                me.acc_unit[buf] = (u, gi)
                 engine.append(("commit", [c.acc_full[buf] for c in ctas]))
-                for c in ctas:
-                    c.acc_full[buf].arrive()      # the issuing thread's own arrive (remote for the odd CTA)
+                if pair:
+                    me.hand_full[buf].arrive()    # to the relay
+                me.acc_full[buf].arrive()         # the issuing thread's own arrive
                 aph[buf] ^= 1
                 buf ^= 1
+
+    def relay():
+        me, odd = ctas[0], ctas[1]
+        hb = 0
+        hph = [0, 0]
+        while True:
+            yield from wait(me.hand_full[hb], hph[hb])
+            tag = me.acc_unit[hb]
+            if relay_early:
+                odd.acc_full[hb].arrive()
+                yield "step"
+                odd.acc_unit[hb] = tag
+            else:
+                odd.acc_unit[hb] = tag        # remote store, ordered by the release arrive
+                odd.acc_full[hb].arrive()
+            if tag == "end":
+                odd.acc_full[hb].arrive()
+                return
+            hph[hb] ^= 1
+            hb ^= 1
 
     def epilogue(r):
         cta = ctas[r]
@@ -221,10 +266,10 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
 
     def run_engine(op):
         if op[0] == "mma":
-            _, st, ab, want, buf, gi = op
+            _, st, (ab, half), want, buf, gi = op
             for c in ctas:
                 assert c.stage[st] == want, "MMA read a stale stage"
-                assert c.abuf[ab] == want, "MMA read a stale A buffer"
+                assert c.abuf[ab][half] == want, "MMA read a stale A buffer"
                 prev = c.acc[buf]
                 c.acc[buf] = (want[0], gi)
                 assert prev in (None, (want[0], gi)), "accumulator overwritten before it was read"
@@ -236,6 +281,8 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
     for r in range(len(ctas)):
         actors += [producer(r), converter(r, 0), converter(r, 1), epilogue(r)]
     actors.append(mma())
+    if pair:
+        actors.append(relay())
     alive = list(actors)
     idle = 0
     while alive or copies or engine:
@@ -273,9 +320,10 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False):
 
 @pytest.mark.parametrize("pair,ns", [(False, 4), (True, 6), (True, 4), (False, 6), (True, 8)])
 @pytest.mark.parametrize("n_units,kch", [(0, 3), (1, 3), (5, 3), (3, 16), (7, 9)])
-def test_protocol_random_interleavings(pair, ns, n_units, kch):
+@pytest.mark.parametrize("kpb", [1, 2])
+def test_protocol_random_interleavings(pair, ns, n_units, kch, kpb):
     for seed in range(30):
-        run_model(pair, ns, n_units, kch, 8, seed)
+        run_model(pair, ns, n_units, kch, 8, seed, kpb=kpb)
 
 
 def test_sentinel_without_buffer_wait_is_caught():
@@ -285,14 +333,15 @@ def test_sentinel_without_buffer_wait_is_caught():
     bad = 0
     for seed in range(60):
         try:
-            run_model(True, 6, 1, 3, 8, seed, skip_aempty=True)
+            run_model(True, 6, 1, 3, 8, seed, skip_aempty=True, kpb=1)
         except AssertionError:
             bad += 1
     assert bad > 0
 
 
 @pytest.mark.parametrize("pair", [False, True])
-def test_odd_stage_count_is_caught(pair):
+@pytest.mark.parametrize("kpb", [1, 2])
+def test_odd_stage_count_is_caught(pair, kpb):
     """Sensitivity: with an odd number of stages, k-chunk i - NS belongs to the
     other converter set, so a set can reach chunk i before the stage's
     previous copy has landed and pass its parity wait on the earlier phase
@@ -300,7 +349,35 @@ def test_odd_stage_count_is_caught(pair):
     bad = 0
     for seed in range(40):
         try:
-            run_model(pair, 5, 5, 3, 8, seed)
+            run_model(pair, 5, 5, 3, 8, seed, kpb=kpb)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_buffer_count_of_one_set_is_caught(pair):
+    """Sensitivity: with two k-chunks per A buffer, an afull count that covers
+    one converter set only (the count of one-k-chunk buffers) lets the MMA
+    thread read the second part of a buffer before the other set has written
+    it."""
+    bad = 0
+    for seed in range(40):
+        try:
+            run_model(pair, 4 if not pair else 6, 3, 5, 8, seed, kpb=2, afull_sets=1)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
+
+
+def test_relay_arriving_before_the_tag_is_caught():
+    """Sensitivity: a relay whose arrive on the odd CTA's acc_full is not
+    ordered after the tag store (a relaxed arrive) lets the odd epilogue read
+    the previous group's tag."""
+    bad = 0
+    for seed in range(60):
+        try:
+            run_model(True, 6, 3, 9, 2, seed, kpb=2, relay_early=True)
         except AssertionError:
             bad += 1
     assert bad > 0
