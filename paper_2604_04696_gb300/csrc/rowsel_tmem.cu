@@ -71,7 +71,6 @@ constexpr int T_FLUSH = 4;                           // groups summed before one
 constexpr int T_RAW_TILE = T_MROWS * T_KCHUNK * 4;   // 8 KB ring tile
 constexpr int T_B_TILE = T_NDIG * T_KCHUNK * 2;      // 24 KB
 constexpr int T_ABUF_MAX = 4;                        // A buffer barriers reserved
-constexpr uint32_t T_PREF = 8;                       // L2 prefetch distance, in k-chunks
 constexpr uint32_t T_ACC_COLS = T_NDIG;
 constexpr uint32_t T_A_COL0 = 2 * T_ACC_COLS;        // 384
 constexpr uint32_t T_TMEM_COLS = 512;
@@ -90,27 +89,34 @@ static_assert(W_CONV0 % 4 == 0 && W_EPI0 % 4 == 0, "tensor-memory roles start on
 constexpr int T_TASK_CLIENTS = T_MROWS / 2;         // clients of one ingest task (one m-block)
 constexpr int T_OUT_BYTES = T_MROWS * T_NCOLS * 4;   // 8 KB
 
-// Shared-memory stages (B tile part + ring tile) are decoupled from the
-// tensor-memory A buffers: k-chunk i of a CTA uses stage i % NS and part
-// i % KPB of A buffer (i / KPB) % NBUF. The ingest loads its task's 64 KB of
+// Shared memory holds NS B stages (this CTA's part of a database tile) and RS
+// ring slots (a ring tile each), filled and released separately: k-chunk i of
+// a CTA uses B stage i % NS (freed by the commit of its MMAs), ring slot i % RS
+// (freed by its converters as soon as they have read it) and part i % KPB of
+// tensor-memory A buffer (i / KPB) % NBUF. The ingest loads its task's 64 KB of
 // raw residues as 16 / BOX_CLIENTS boxes into one box buffer, so a smaller box
 // leaves room for more stages.
 template <bool PAIR>
 struct TmemCfg {
   static constexpr int B_BYTES = PAIR ? T_B_TILE / 2 : T_B_TILE;   // this CTA's part of B
-  static constexpr int STAGE = T_RAW_TILE + B_BYTES;
   static constexpr int KPB = PAIR ? 2 : 1;                          // k-chunks per A buffer
   static constexpr int NBUF = 4 / KPB;                              // A buffers (128 columns)
   static constexpr int BOX_CLIENTS = PAIR ? 8 : 16;                 // clients per ingest box
   static constexpr int RAW_BOX = BOX_CLIENTS * T_KCHUNK * 2 * 8 * 4;   // x 64 k x 2 x 8 slots x 4 B
-  static constexpr int NS = PAIR ? 8 : 4;
-  static constexpr size_t SMEM = 1024 + (size_t)NS * STAGE + RAW_BOX + T_OUT_BYTES + 1024;
+  static constexpr int NS = PAIR ? 8 : 4;                           // B stages
+  static constexpr int RS = PAIR ? 8 : 6;                           // ring slots
+  static constexpr size_t SMEM =
+      1024 + (size_t)NS * B_BYTES + (size_t)RS * T_RAW_TILE + RAW_BOX + T_OUT_BYTES + 1024;
   static_assert(KPB == 1 || KPB == 2, "an A buffer holds one k-chunk or one of each converter set");
   static_assert(T_TASK_CLIENTS % BOX_CLIENTS == 0 && BOX_CLIENTS % 4 == 0, "whole boxes per ingest task");
-  // Even: a converter set waits full[stage] for k-chunks i, i + 2, ...; the
-  // stage's previous k-chunk i - NS must then be one the same set has already
-  // waited for, else a parity wait could pass on the phase before it.
-  static_assert(NS % 2 == 0, "two converter sets need an even number of stages");
+  // A converter set waits on the ring slots of k-chunks i, i + 2, ...: the
+  // slot's previous k-chunk i - RS must be one the same set has already waited
+  // for (RS even), else a parity wait could pass on the phase before it. For
+  // the B stage of k-chunk i it first waits for its A buffer's previous use,
+  // whose MMAs (k-chunk i - 4 and earlier) follow the landing of B stage use
+  // i - NS when NS >= 4: any such count is safe.
+  static_assert(RS % 2 == 0, "two converter sets need an even number of ring slots");
+  static_assert(NS >= NBUF * KPB, "a B stage's previous use must precede the A buffer's");
 };
 static_assert(TmemCfg<false>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
 static_assert(TmemCfg<true>::SMEM <= 232448, "tensor-memory kernel shared memory exceeds 227 KB");
@@ -196,11 +202,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
       "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
-}
-
-// Prefetch [src, src + bytes) into L2 (bytes a multiple of 16).
-__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Three loads of 4 columns each (the three database digits of 4 columns).
@@ -326,22 +327,26 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   using Cfg = TmemCfg<PAIR>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // stage st: B part at smem + st * STAGE (1024-aligned), ring tile after it
-  constexpr int NS = Cfg::NS;
-  uint8_t *rawbox = smem + NS * Cfg::STAGE;
+  // B stage st at smem + st * B_BYTES (1024-aligned), then the ring slots
+  constexpr int NS = Cfg::NS, RS = Cfg::RS;
+  uint8_t *rslots = smem + NS * Cfg::B_BYTES;
+  uint8_t *rawbox = rslots + RS * T_RAW_TILE;
   uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + Cfg::RAW_BOX);
-  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + Cfg::RAW_BOX + T_OUT_BYTES);
-  uint64_t *empty = full + NS;
-  uint64_t *afull = empty + NS;                   // [NBUF] A buffer converted (pair: both CTAs')
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + Cfg::RAW_BOX + T_OUT_BYTES);   // [NS] B part landed
+  uint64_t *empty = full + NS;                    // [NS] B part read by its MMAs
+  uint64_t *rfull = empty + NS;                   // [RS] ring tile landed
+  uint64_t *rempty = rfull + RS;                  // [RS] ring tile read by its converters
+  uint64_t *afull = rempty + RS;                  // [NBUF] A buffer converted (pair: both CTAs')
   uint64_t *aempty = afull + T_ABUF_MAX;          // [NBUF] A buffer read by its MMAs
   uint64_t *acc_full = aempty + T_ABUF_MAX;
   uint64_t *acc_empty = acc_full + 2;
   uint64_t *box_bar = acc_empty + 2;
   uint64_t *ostage_full = box_bar + 1;
   uint64_t *ostage_empty = ostage_full + 1;
-  uint64_t *stage_unit = ostage_empty + 1;        // [NS]
-  uint64_t *stage_kc = stage_unit + NS;           // [NS] k-chunk of the unit in the stage
-  uint64_t *acc_unit = stage_kc + NS;             // [2]
+  uint64_t *stage_unit = ostage_empty + 1;        // [NS] unit of the B stage
+  uint64_t *slot_unit = stage_unit + NS;          // [RS] unit of the ring slot
+  uint64_t *slot_kc = slot_unit + RS;             // [RS] k-chunk of the unit in the ring slot
+  uint64_t *acc_unit = slot_kc + RS;              // [2]
   uint64_t *task_slot = acc_unit + 2;
   uint64_t *ostage_unit = task_slot + 1;
   uint64_t *mail = ostage_unit + 1;               // pair: [4] claimed units, even -> odd CTA
@@ -350,6 +355,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   uint64_t *hand_full = mail_empty + 4;           // pair (even CTA): [2] group handed to the relay
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hand_full + 2);
   volatile uint32_t *abort_flag = tmem_slot + 1;
+  // barriers and tags above, in 8-byte words, within the 1 KB reserved for them
+  static_assert(8 * (3 * NS + 4 * RS + 2 * T_ABUF_MAX + 4 + 3 + 2 + 2 + 12 + 2 + 1) <= 1024,
+                "tensor-memory kernel barrier area exceeds its reservation");
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
@@ -357,6 +365,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     for (int s2 = 0; s2 < NS; ++s2) {
       mbar_init(&full[s2], 1);
       mbar_init(&empty[s2], 1);
+    }
+    for (int r = 0; r < RS; ++r) {
+      mbar_init(&rfull[r], 1);
+      mbar_init(&rempty[r], 4);   // the 4 warps of the converter set that read it
     }
     for (int a = 0; a < Cfg::NBUF; ++a) {
       // the 4 warps of each converter set filling the buffer (KPB sets); in
@@ -474,11 +486,13 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
 
   if (warp == W_PROD) {
     // ---------------- producer: claims units, copies ring + B tiles ----------------
-    // Claims one unit ahead and prefetches into L2 the tiles T_PREF stages
-    // ahead (the rest of this unit, then the next unit's), so that the bulk
-    // copies on the critical path hit L2.
+    // Claims one unit ahead, so that a claim (a global atomic, and in the pair
+    // the mailbox round trip) is off the copy path. Per k-chunk: the ring tile
+    // into the next ring slot once its converters have read it, then the B
+    // part into the next B stage once its MMAs have run.
     if (lane == 0) {
-      uint32_t st = 0, ph = 0, mi = 0;
+      uint32_t st = 0, ph = 0, r = 0, rph = 0, mi = 0;
+      uint32_t b_issued = 0, b_ph = 0, r_issued = 0, r_ph = 0;   // copies issued, parity of the last one
       bool ok = true;
       auto claim = [&](uint64_t &u) -> bool {
         if constexpr (PAIR) {
@@ -501,70 +515,65 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         }
         return true;
       };
-      struct Src {
-        const uint8_t *a, *b;
-        uint64_t E;
+      auto next_stage = [&]() {
+        if (++st == NS) {
+          st = 0;
+          ph ^= 1u;
+        }
       };
-      auto sources = [&](uint64_t u) -> Src {
-        Src r;
-        r.E = entry_of(u);
-        const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-        const uint32_t g = (uint32_t)(r.E / p.mblk);
-        const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        r.a = p.ring + (((r.E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
-        r.b = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
-              (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
-        return r;
+      auto next_slot = [&]() {
+        if (++r == RS) {
+          r = 0;
+          rph ^= 1u;
+        }
       };
       uint64_t u = kNoUnit, un = kNoUnit;
       ok = claim(u);
       if (ok && u != kNoUnit) ok = claim(un);
       while (ok && u != kNoUnit) {
-        const Src sc = sources(u);
-        const bool has_next = un != kNoUnit;
-        const Src sn = has_next ? sources(un) : sc;
-        const uint32_t ready_next = (uint32_t)((sn.E / p.R + 1) * p.kch);
-        bool next_ready = false;
-        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[sc.E % p.R], (uint32_t)((sc.E / p.R + 1) * p.kch)))))
+        const uint64_t E = entry_of(u);
+        const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
+        const uint32_t g = (uint32_t)(E / p.mblk);
+        const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
+        const uint8_t *src_a = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
+        const uint8_t *src_b = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
+                               (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
+        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch)))))
           break;
         fence_proxy_async_global();
         for (uint32_t kc = 0; kc < p.kch; ++kc) {
-          const uint32_t k2 = kc + T_PREF;
-          if (k2 < p.kch) {
-            prefetch_l2(sc.b + (uint64_t)k2 * T_B_TILE, Cfg::B_BYTES);
-            prefetch_l2(sc.a + (uint64_t)k2 * T_RAW_TILE, T_RAW_TILE);
-          } else if (has_next && k2 - p.kch < p.kch) {
-            const uint32_t k3 = k2 - p.kch;
-            prefetch_l2(sn.b + (uint64_t)k3 * T_B_TILE, Cfg::B_BYTES);
-            if (!next_ready) next_ready = ld_acquire(&p.ready[sn.E % p.R]) >= ready_next;
-            if (next_ready) prefetch_l2(sn.a + (uint64_t)k3 * T_RAW_TILE, T_RAW_TILE);
-          }
+          if (!(ok = TM_TIMED(kTPWaitEmpty, wait(&rempty[r], rph ^ 1u, kErrTmaWait)))) break;
+          slot_unit[r] = u;
+          slot_kc[r] = kc;
+          mbar_arrive_expect_tx(&rfull[r], T_RAW_TILE);
+          bulk_g2s(rslots + r * T_RAW_TILE, src_a + (uint64_t)kc * T_RAW_TILE, T_RAW_TILE, &rfull[r]);
+          r_issued |= 1u << r;
+          r_ph = (r_ph & ~(1u << r)) | (rph << r);
+          next_slot();
           if (!(ok = TM_TIMED(kTPWaitEmpty, wait(&empty[st], ph ^ 1u, kErrTmaWait)))) break;
           stage_unit[st] = u;
-          stage_kc[st] = kc;
-          uint8_t *sb = smem + st * Cfg::STAGE;
-          mbar_arrive_expect_tx(&full[st], Cfg::STAGE);
-          bulk_g2s(sb, sc.b + (uint64_t)kc * T_B_TILE, Cfg::B_BYTES, &full[st]);
-          bulk_g2s(sb + Cfg::B_BYTES, sc.a + (uint64_t)kc * T_RAW_TILE, T_RAW_TILE, &full[st]);
-          if (++st == NS) {
-            st = 0;
-            ph ^= 1u;
-          }
+          mbar_arrive_expect_tx(&full[st], Cfg::B_BYTES);
+          bulk_g2s(smem + st * Cfg::B_BYTES, src_b + (uint64_t)kc * T_B_TILE, Cfg::B_BYTES, &full[st]);
+          b_issued |= 1u << st;
+          b_ph = (b_ph & ~(1u << st)) | (ph << st);
+          next_stage();
         }
         if (!ok) break;
         u = un;
         un = kNoUnit;
         if (u != kNoUnit) ok = claim(un);
       }
-      // end of work: a sentinel in the next two stages, one for each converter set
+      // end of work: a sentinel in the next two k-chunks, one for each
+      // converter set; the B stage's tag is written first, so that the ring
+      // slot's arrive (a release) publishes it to the MMA thread too
       for (int k = 0; k < 2 && ok; ++k) {
         if (!(ok = wait(&empty[st], ph ^ 1u, kErrTmaWait))) break;
         stage_unit[st] = kNoUnit;
-        mbar_arrive(&full[st]);
-        if (++st == NS) {
-          st = 0;
-          ph ^= 1u;
-        }
+        next_stage();
+        if (!(ok = wait(&rempty[r], rph ^ 1u, kErrTmaWait))) break;
+        slot_unit[r] = kNoUnit;
+        mbar_arrive(&rfull[r]);
+        next_slot();
       }
       if (ok) {
         if constexpr (PAIR) {
@@ -572,14 +581,15 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           // let them land on the other stages before the CTA leaves
           for (int s2 = 2; s2 < NS; ++s2) {
             mbar_wait_bounded(&empty[st], ph ^ 1u, nullptr, 0);
-            if (++st == NS) {
-              st = 0;
-              ph ^= 1u;
-            }
+            next_stage();
           }
         }
       } else {
-        for (int s2 = 0; s2 < NS; ++s2) mbar_wait_bounded(&empty[s2], ph ^ 1u, nullptr, 0);
+        // let this CTA's copies in flight land before it leaves
+        for (int s2 = 0; s2 < NS; ++s2)
+          if ((b_issued >> s2) & 1u) mbar_wait_bounded(&full[s2], (b_ph >> s2) & 1u, nullptr, 0);
+        for (int r2 = 0; r2 < RS; ++r2)
+          if ((r_issued >> r2) & 1u) mbar_wait_bounded(&rfull[r2], (r_ph >> r2) & 1u, nullptr, 0);
       }
     }
   } else if (warp >= W_CONV0 && warp < W_CONV0 + N_CONV) {
@@ -597,13 +607,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     for (uint32_t it = 0;; ++it) {
       const uint32_t i = 2u * it + cs;                      // this CTA's k-chunk sequence number
       const uint32_t st = i % NS, ph = (i / NS) & 1u;
+      const uint32_t r = i % RS, rph = (i / RS) & 1u;
       const uint32_t bi = i / Cfg::KPB, ab = bi % Cfg::NBUF, aph = (bi / Cfg::NBUF) & 1u;
       const uint32_t acol = T_A_COL0 + ab * (32u * Cfg::KPB) + (i % Cfg::KPB) * 32u;
-      const bool okf = conv_counter ? TM_TIMED(kTCWaitFull, wait(&full[st], ph, kErrTmaWait))
-                                    : wait(&full[st], ph, kErrTmaWait);
+      const bool okf = conv_counter ? TM_TIMED(kTCWaitFull, wait(&rfull[r], rph, kErrTmaWait))
+                                    : wait(&rfull[r], rph, kErrTmaWait);
       if (!__all_sync(0xffffffffu, okf)) break;
       const uint64_t tconv = PROF ? clock64() : 0;
-      const uint64_t un = stage_unit[st];
+      const uint64_t un = slot_unit[r];
       if (un == kNoUnit) {
         // Wait for the A buffer's previous k-chunk to be read by its MMAs even
         // here: in the pair form an early sentinel arrival could complete the
@@ -620,10 +631,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         break;
       }
       // the unit's last ring tile is in shared memory: its ring entry may be reused
-      if (qw == 0 && lane == 0 && stage_kc[st] + 1 == p.kch) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
+      if (qw == 0 && lane == 0 && slot_kc[r] + 1 == p.kch) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
       // this thread's digit plane: 8 bytes per k octet (conflict-free: the
       // warp's 32 reads of a step cover every bank twice)
-      const uint2 *row = reinterpret_cast<const uint2 *>(smem + st * Cfg::STAGE + Cfg::B_BYTES) + m * 32;
+      const uint2 *row = reinterpret_cast<const uint2 *>(rslots + r * T_RAW_TILE) + m * 32;
       uint32_t wv[32];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -633,11 +644,17 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         wv[4 * j + 2] = plane_pair(z.y, 0x5140u);
         wv[4 * j + 3] = plane_pair(z.y, 0x5342u);
       }
+      // the digits are in registers (every loaded word went into them): the
+      // ring slot may be refilled
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rempty[r]);
       const uint64_t tst = PROF ? clock64() : 0;
       if (conv_counter) pc[PROF ? kTCBusy : 0] += tst - tconv;
-      // the digits are in registers; the A buffer's previous k-chunk must have
-      // been read by its MMAs before they overwrite it
+      // the A buffer's previous k-chunk must have been read by its MMAs before
+      // the digits overwrite it, and the MMAs of this k-chunk also read the B
+      // stage: signal the buffer only once that has landed
       if (!__all_sync(0xffffffffu, wait(&aempty[ab], aph ^ 1u, kErrMmaWait))) break;
+      if (!__all_sync(0xffffffffu, wait(&full[st], ph, kErrTmaWait))) break;
       tc_fence_after();
       tmem_st32(lane_base + acol, wv);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -695,7 +712,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
             first = false;
             tc_fence_after();
             const uint64_t tiss = PROF ? clock64() : 0;
-            const uint32_t sb = smem_u32(smem + st * Cfg::STAGE);
+            const uint32_t sb = smem_u32(smem + st * Cfg::B_BYTES);
             const uint32_t ab = (i / Cfg::KPB) % Cfg::NBUF;
             const bool a_done = i % Cfg::KPB == Cfg::KPB - 1;
             const uint32_t ta = tmem_base + T_A_COL0 + ab * (32u * Cfg::KPB) + (i % Cfg::KPB) * 32u;

@@ -5,18 +5,21 @@ interleavings.
 The model restates the kernel's rules with exact mbarrier semantics (arrival
 count, transaction bytes, phase parity; no code shared with the CUDA source):
   - the producer of each CTA claims units one ahead (the pair's odd CTA
-    receives them through a mailbox), fills shared-memory stage i % NS (NS
-    even) for
-    its i-th k-chunk after empty[stage] (arrive.expect_tx on full[stage]; the
-    copies land asynchronously), and ends with a sentinel in two consecutive
-    stages, one per converter set; the pair's producers then wait for the
-    commits of their other stages;
+    receives them through a mailbox); for its i-th k-chunk it copies the ring
+    tile into ring slot i % RS after rempty[slot] (arrive.expect_tx on
+    rfull[slot]) and the B part into B stage i % NS after empty[stage]
+    (expect_tx on full[stage]; RS, NS even; the copies land asynchronously,
+    in any order), and ends with a sentinel in two consecutive k-chunks, one
+    per converter set, the B stage's tag written before the slot's arrive;
+    the pair's producers then wait for the commits of their other stages;
   - k-chunk i goes into part i % KPB of A buffer (i // KPB) % NBUF (KPB = 1:
     four buffers of one k-chunk; KPB = 2: two buffers of two); converter set
     c (two sets of four warps) takes k-chunks i = c, c + 2, ...: it waits
-    full[stage], waits aempty of its buffer (the buffer's previous k-chunks
-    read by their MMAs; also before a sentinel), stops at a sentinel after
-    arriving on afull, else writes its part and arrives on afull (count
+    rfull[slot], stops at a sentinel (after waiting aempty of its buffer, the
+    buffer's previous k-chunks read by their MMAs, and arriving on afull),
+    else reads the ring tile, arrives on rempty[slot], waits aempty and
+    full[stage] (the MMAs read the B part too), writes its part and arrives
+    on afull (count
     4 KPB; in the pair, both CTAs' sets arrive on the even CTA's afull, count
     8 KPB);
   - the (even CTA's) MMA thread waits afull at the first part of a buffer
@@ -69,15 +72,19 @@ class Bar:
 
 
 class Cta:
-    def __init__(self, ns, nbuf, afull_count, acc_empty_count):
+    def __init__(self, ns, rs, nbuf, afull_count, acc_empty_count):
         self.full = [Bar(1) for _ in range(ns)]
         self.empty = [Bar(1) for _ in range(ns)]
+        self.rfull = [Bar(1) for _ in range(rs)]
+        self.rempty = [Bar(4) for _ in range(rs)]
+        self.slot = [None] * rs             # ring tile in the slot: (unit, kc) once landed
+        self.slot_unit = [None] * rs
         self.afull = [Bar(afull_count) for _ in range(nbuf)]
         self.aempty = [Bar(1) for _ in range(nbuf)]
         self.acc_full = [Bar(2) for _ in range(2)]
         self.acc_empty = [Bar(acc_empty_count) for _ in range(2)]
         self.hand_full = [Bar(1) for _ in range(2)]
-        self.stage = [None] * ns            # data in the stage: (unit, kc) once landed
+        self.stage = [None] * ns            # B part in the stage: (unit, kc) once landed
         self.stage_unit = [None] * ns
         self.abuf = [[None, None] for _ in range(nbuf)]  # (unit, kc) converted into each part
         self.acc_unit = [None] * 2
@@ -86,14 +93,15 @@ class Cta:
 
 
 def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, afull_sets=None,
-              relay_early=False):
+              relay_early=False, rs=None, early_release=False, skip_b_wait=False):
     rng = random.Random(seed)
     nbuf = 4 // kpb
+    rs = ns if rs is None else rs
     sets = kpb if afull_sets is None else afull_sets
     if pair:
-        ctas = [Cta(ns, nbuf, 8 * sets, 2 * EPI), Cta(ns, nbuf, 4 * sets, EPI)]
+        ctas = [Cta(ns, rs, nbuf, 8 * sets, 2 * EPI), Cta(ns, rs, nbuf, 4 * sets, EPI)]
     else:
-        ctas = [Cta(ns, nbuf, 4 * sets, EPI)]
+        ctas = [Cta(ns, rs, nbuf, 4 * sets, EPI)]
     mail, mail_full, mail_empty = [None] * 4, [Bar(1) for _ in range(4)], [Bar(1) for _ in range(4)]
     claims = [0]
     copies = []
@@ -107,6 +115,7 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
     def producer(r):
         cta = ctas[r]
         st = ph = 0
+        sl = sph = 0
         mi = [0]
 
         def claim():
@@ -136,11 +145,17 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
         un = (yield from get()) if u is not None else None
         while u is not None:
             for kc in range(kch):
+                yield from wait(cta.rempty[sl], sph ^ 1)
+                cta.slot_unit[sl] = (u, kc)
+                cta.slot[sl] = None
+                cta.rfull[sl].arrive(tx=1)
+                copies.append((cta, "slot", sl, (u, kc)))
+                sl, sph = (sl + 1) % rs, sph ^ (sl + 1 == rs)
                 yield from wait(cta.empty[st], ph ^ 1)
                 cta.stage_unit[st] = (u, kc)
                 cta.stage[st] = None
                 cta.full[st].arrive(tx=1)
-                copies.append((cta, st, (u, kc)))
+                copies.append((cta, "stage", st, (u, kc)))
                 st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
             u, un = un, None
             if u is not None:
@@ -148,8 +163,11 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
         for _ in range(2):
             yield from wait(cta.empty[st], ph ^ 1)
             cta.stage_unit[st] = "end"
-            cta.full[st].arrive()
             st, ph = (st + 1) % ns, ph ^ (st + 1 == ns)
+            yield from wait(cta.rempty[sl], sph ^ 1)
+            cta.slot_unit[sl] = "end"
+            cta.rfull[sl].arrive()
+            sl, sph = (sl + 1) % rs, sph ^ (sl + 1 == rs)
         if pair:
             for _ in range(2, ns):
                 yield from wait(cta.empty[st], ph ^ 1)
@@ -162,10 +180,11 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
         while True:
             i = 2 * it + cs
             st, ph = i % ns, (i // ns) & 1
+            sl, sph = i % rs, (i // rs) & 1
             bi = i // kpb
             ab, aph, part = bi % nbuf, (bi // nbuf) & 1, i % kpb
-            yield from wait(cta.full[st], ph)
-            tag = cta.stage_unit[st]
+            yield from wait(cta.rfull[sl], sph)
+            tag = cta.slot_unit[sl]
             # the A buffer's previous pair of k-chunks must have been read by
             # its MMAs, also before a sentinel: an early sentinel arrival would
             # complete the afull phase of that previous pair without the other
@@ -175,7 +194,14 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
             if tag == "end":
                 target.afull[ab].arrive(4)
                 return
-            assert cta.stage[st] == tag, "converter read a stage that has not landed"
+            if early_release:
+                cta.rempty[sl].arrive(4)
+                yield "step"
+            assert cta.slot[sl] == tag, "converter read a ring slot that has not landed or was refilled"
+            if not early_release:
+                cta.rempty[sl].arrive(4)
+            if not skip_b_wait:
+                yield from wait(cta.full[st], ph)
             cta.abuf[ab][part] = tag
             target.afull[ab].arrive(4)
             it += 1
@@ -268,7 +294,7 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
         if op[0] == "mma":
             _, st, (ab, half), want, buf, gi = op
             for c in ctas:
-                assert c.stage[st] == want, "MMA read a stale stage"
+                assert c.stage[st] == want, "MMA read a stale B stage"
                 assert c.abuf[ab][half] == want, "MMA read a stale A buffer"
                 prev = c.acc[buf]
                 c.acc[buf] = (want[0], gi)
@@ -289,9 +315,13 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
         kinds = ["actor"] * len(alive) + (["copy"] if copies else []) + (["engine"] if engine else [])
         k = rng.randrange(len(kinds))
         if kinds[k] == "copy":
-            cta, st, tag = copies.pop(rng.randrange(len(copies)))
-            cta.stage[st] = tag
-            cta.full[st].complete_tx(1)
+            cta, kind, k, tag = copies.pop(rng.randrange(len(copies)))
+            if kind == "slot":
+                cta.slot[k] = tag
+                cta.rfull[k].complete_tx(1)
+            else:
+                cta.stage[k] = tag
+                cta.full[k].complete_tx(1)
             idle = 0
         elif kinds[k] == "engine":
             run_engine(engine.pop(0))
@@ -318,12 +348,12 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
     return True
 
 
-@pytest.mark.parametrize("pair,ns", [(False, 4), (True, 6), (True, 4), (False, 6), (True, 8)])
+@pytest.mark.parametrize("pair,ns,rs", [(False, 4, 6), (True, 8, 8), (True, 4, 6), (False, 6, 4), (True, 6, 10)])
 @pytest.mark.parametrize("n_units,kch", [(0, 3), (1, 3), (5, 3), (3, 16), (7, 9)])
 @pytest.mark.parametrize("kpb", [1, 2])
-def test_protocol_random_interleavings(pair, ns, n_units, kch, kpb):
+def test_protocol_random_interleavings(pair, ns, rs, n_units, kch, kpb):
     for seed in range(30):
-        run_model(pair, ns, n_units, kch, 8, seed, kpb=kpb)
+        run_model(pair, ns, n_units, kch, 8, seed, kpb=kpb, rs=rs)
 
 
 def test_sentinel_without_buffer_wait_is_caught():
@@ -341,15 +371,26 @@ def test_sentinel_without_buffer_wait_is_caught():
 
 @pytest.mark.parametrize("pair", [False, True])
 @pytest.mark.parametrize("kpb", [1, 2])
-def test_odd_stage_count_is_caught(pair, kpb):
-    """Sensitivity: with an odd number of stages, k-chunk i - NS belongs to the
-    other converter set, so a set can reach chunk i before the stage's
+def test_odd_b_stage_count_is_safe(pair, kpb):
+    """A converter waits for its A buffer's previous use (the MMAs of k-chunk
+    i - 4 and earlier) before the B stage of k-chunk i, so the stage's
+    previous use i - NS has landed for any NS >= 4, odd or even."""
+    for seed in range(30):
+        run_model(pair, 5, 5, 9, 8, seed, kpb=kpb, rs=4)
+
+
+@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("kpb", [1, 2])
+@pytest.mark.parametrize("odd", ["slots"])
+def test_odd_stage_count_is_caught(pair, kpb, odd):
+    """Sensitivity: with an odd number of ring slots, k-chunk i - RS belongs
+    to the other converter set, so a set can reach chunk i before the slot's
     previous copy has landed and pass its parity wait on the earlier phase
     (why the kernel requires an even count)."""
     bad = 0
-    for seed in range(40):
+    for seed in range(60):
         try:
-            run_model(pair, 5, 5, 3, 8, seed, kpb=kpb)
+            run_model(pair, 4, 5, 9, 8, seed, kpb=kpb, rs=5)
         except AssertionError:
             bad += 1
     assert bad > 0
@@ -378,6 +419,32 @@ def test_relay_arriving_before_the_tag_is_caught():
     for seed in range(60):
         try:
             run_model(True, 6, 3, 9, 2, seed, kpb=2, relay_early=True)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_ring_slot_released_before_its_read_is_caught(pair):
+    """Sensitivity: releasing a ring slot before the converters have read it
+    lets the producer refill it under them."""
+    bad = 0
+    for seed in range(40):
+        try:
+            run_model(pair, 4, 3, 9, 8, seed, rs=2, early_release=True)
+        except AssertionError:
+            bad += 1
+    assert bad > 0
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_converter_skipping_the_b_stage_wait_is_caught(pair):
+    """Sensitivity: signalling an A buffer without waiting for the k-chunk's B
+    stage lets the MMAs read a B part still in flight."""
+    bad = 0
+    for seed in range(40):
+        try:
+            run_model(pair, 4, 3, 5, 8, seed, rs=6, skip_b_wait=True)
         except AssertionError:
             bad += 1
     assert bad > 0
