@@ -101,12 +101,12 @@ struct TmemCfg {
   static constexpr int B_BYTES = PAIR ? T_B_TILE / 2 : T_B_TILE;   // this CTA's part of B
   static constexpr int KPB = PAIR ? 2 : 1;                          // k-chunks per A buffer
   static constexpr int NBUF = 4 / KPB;                              // A buffers (128 columns)
-  static constexpr int BOX_CLIENTS = PAIR ? 8 : 16;                 // clients per ingest box
+  static constexpr int BOX_CLIENTS = 8;                             // clients per ingest box (two buffers)
   static constexpr int RAW_BOX = BOX_CLIENTS * T_KCHUNK * 2 * 8 * 4;   // x 64 k x 2 x 8 slots x 4 B
   static constexpr int NS = PAIR ? 8 : 4;                           // B stages
-  static constexpr int RS = PAIR ? 8 : 6;                           // ring slots
+  static constexpr int RS = 6;                                      // ring slots
   static constexpr size_t SMEM =
-      1024 + (size_t)NS * B_BYTES + (size_t)RS * T_RAW_TILE + RAW_BOX + T_OUT_BYTES + 1024;
+      1024 + (size_t)NS * B_BYTES + (size_t)RS * T_RAW_TILE + 2 * (size_t)RAW_BOX + T_OUT_BYTES + 1024;
   static_assert(KPB == 1 || KPB == 2, "an A buffer holds one k-chunk or one of each converter set");
   static_assert(T_TASK_CLIENTS % BOX_CLIENTS == 0 && BOX_CLIENTS % 4 == 0, "whole boxes per ingest task");
   // A converter set waits on the ring slots of k-chunks i, i + 2, ...: the
@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   constexpr int NS = Cfg::NS, RS = Cfg::RS;
   uint8_t *rslots = smem + NS * Cfg::B_BYTES;
   uint8_t *rawbox = rslots + RS * T_RAW_TILE;
-  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + Cfg::RAW_BOX);
-  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + Cfg::RAW_BOX + T_OUT_BYTES);   // [NS] B part landed
+  uint32_t *out_stage = reinterpret_cast<uint32_t *>(rawbox + 2 * Cfg::RAW_BOX);
+  uint64_t *full = reinterpret_cast<uint64_t *>(rawbox + 2 * Cfg::RAW_BOX + T_OUT_BYTES);   // [NS] B part landed
   uint64_t *empty = full + NS;                    // [NS] B part read by its MMAs
   uint64_t *rfull = empty + NS;                   // [RS] ring tile landed
   uint64_t *rempty = rfull + RS;                  // [RS] ring tile read by its converters
@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   uint64_t *aempty = afull + T_ABUF_MAX;          // [NBUF] A buffer read by its MMAs
   uint64_t *acc_full = aempty + T_ABUF_MAX;
   uint64_t *acc_empty = acc_full + 2;
-  uint64_t *box_bar = acc_empty + 2;
-  uint64_t *ostage_full = box_bar + 1;
+  uint64_t *box_bar = acc_empty + 2;             // [2] ingest box buffer landed
+  uint64_t *ostage_full = box_bar + 2;
   uint64_t *ostage_empty = ostage_full + 1;
   uint64_t *stage_unit = ostage_empty + 1;        // [NS] unit of the B stage
   uint64_t *slot_unit = stage_unit + NS;          // [RS] unit of the ring slot
@@ -353,10 +353,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   uint64_t *mail_full = mail + 4;
   uint64_t *mail_empty = mail_full + 4;
   uint64_t *hand_full = mail_empty + 4;           // pair (even CTA): [2] group handed to the relay
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hand_full + 2);
+  uint64_t *task_ok = hand_full + 2;              // ingest: the current task may write its ring entry
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(task_ok + 1);
   volatile uint32_t *abort_flag = tmem_slot + 1;
   // barriers and tags above, in 8-byte words, within the 1 KB reserved for them
-  static_assert(8 * (3 * NS + 4 * RS + 2 * T_ABUF_MAX + 4 + 3 + 2 + 2 + 12 + 2 + 1) <= 1024,
+  static_assert(8 * (3 * NS + 4 * RS + 2 * T_ABUF_MAX + 4 + 4 + 2 + 2 + 12 + 2 + 1 + 1) <= 1024,
                 "tensor-memory kernel barrier area exceeds its reservation");
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -385,7 +386,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       mbar_init(&mail_empty[i], 1);
     }
     for (int b = 0; b < 2; ++b) mbar_init(&hand_full[b], 1);
-    mbar_init(box_bar, 1);
+    mbar_init(&box_bar[0], 1);
+    mbar_init(&box_bar[1], 1);
     mbar_init(ostage_full, N_EPI);
     mbar_init(ostage_empty, 1);
     *abort_flag = 0;
@@ -921,68 +923,92 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   } else if (warp >= W_ING0) {
     // ---------------- ingest (8 warps, 256 threads) ----------------
     // Task = (entry E, k-chunk kc): 64 KB of raw residues, 8 slots x 32 rows
-    // x 64 k, loaded as 16 / BOX_CLIENTS TMA boxes of BOX_CLIENTS clients,
-    // one after the other into the box buffer. A thread handles (row, k
-    // octet, slot half) items; for each slot it stores the 8 encoded residues
-    // of its row and octet as their four digit planes in two 16-byte chunks of
-    // the slot's ring tile, chunk c16 of row m at position c16 ^ (m % 8).
+    // x 64 k, loaded as 16 / BOX_CLIENTS TMA boxes of BOX_CLIENTS clients
+    // into two box buffers in turn: box g + 1 (the task's next box, or the
+    // next task's first) loads while box g is processed. A task's ring wait
+    // (its entry's previous occupant consumed, the lookahead bound) stays at
+    // its start, after the previous task is published: it may depend on that
+    // task. A thread handles (row, k octet, slot half) items; for each slot it
+    // stores the 8 encoded residues of its row and octet as their four digit
+    // planes in two 16-byte chunks of the slot's ring tile, chunk c16 of row m
+    // at position c16 ^ (m % 8).
     const int it = (warp - W_ING0) * 32 + lane;
     constexpr int NT = 32 * N_ING;
+    constexpr int NPART = T_TASK_CLIENTS / Cfg::BOX_CLIENTS;
     const uint64_t pol_last = l2_policy_evict_last();
-    uint32_t rph = 0;
-    bool issued = false;
-    for (;;) {
-      if (it == 0) {
-        const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
-        *task_slot = (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
-      const uint64_t c = *task_slot;
-      if (c == kNoUnit) break;
-      const uint64_t E = c / p.kch;
-      const uint32_t kc = (uint32_t)(c % p.kch);
+    uint32_t pend = 0, pend_ph = 0;   // thread 0: box buffers loading, parity of their phase
+    auto issue = [&](uint32_t gb, uint64_t task, int part) {
+      // box gb (global box index) of `task`, part `part`, into buffer gb % 2
+      const uint64_t E = task / p.kch;
+      const uint32_t kc = (uint32_t)(task % p.kch);
       const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
-      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      const uint32_t b = gb & 1u;
+      const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
+      uint8_t *dst = rawbox + b * Cfg::RAW_BOX;
+      mbar_arrive_expect_tx(&box_bar[b], Cfg::RAW_BOX);
+      if (p.hints)
+        tma_load_5d_hint(dst, &p.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0,
+                         l2_policy_evict_first());
+      else
+        tma_load_5d(dst, &p.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0);
+      pend |= 1u << b;
+      pend_ph = (pend_ph & ~(1u << b)) | (((gb >> 1) & 1u) << b);
+    };
+    auto claim_task = [&]() -> uint64_t {
+      const uint64_t c = atomicAdd(&p.ctr[1], 1ull);
+      return (c < p.n_tasks && !*abort_flag) ? c : kNoUnit;
+    };
+    if (it == 0) {
+      const uint64_t c = claim_task();
+      if (c != kNoUnit) issue(0, c, 0);
+      *task_slot = c;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    uint64_t c = *task_slot;
+    uint32_t gbox = 0;
+    // Lane = (k octet j, row parity rp, slot half sh): a warp's 16-byte box
+    // reads at step kk cover all 8 bank groups (4 wavefronts per 512 B, the
+    // minimum) because the thread reads k offset kk ^ (j & 1) and slot half
+    // sh = s4 ^ ((j >> 1) & 1); the byte selectors of the plane transpose
+    // undo the swap of k offsets in odd octets.
+    const int j = lane >> 2, rp = (lane >> 1) & 1;
+    const int j0 = j & 1, sh = (lane & 1) ^ ((j >> 1) & 1);
+    const uint32_t sel_a = j0 ? 0x1504u : 0x5140u, sel_b = j0 ? 0x3726u : 0x7362u;
+    uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
+    while (c != kNoUnit) {
+      const uint64_t E = c / p.kch;
+      const uint32_t kc = (uint32_t)(c % p.kch);
+      const uint32_t g = (uint32_t)(E / p.mblk);
+      const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       if (it == 0) {
         const bool near = p.lookahead == 0 || E < p.lookahead ||
                           TM_TIMED(kTIWaitSlot, wait_claims(((E - p.lookahead) >> (PAIR ? 1 : 0)) * p.upe));
-        *task_slot = (near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
-                                                                             (uint32_t)((E / p.R) * p.upe)))))
-                         ? c
-                         : kNoUnit;
+        const bool free = near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
+                                                                                (uint32_t)((E / p.R) * p.upe))));
+        *task_ok = free ? 1u : 0u;   // task_slot may still be read for this task
       }
       asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
-      if (*task_slot == kNoUnit) break;
+      if (*task_ok == 0u) break;
       const uint64_t tbusy = PROF ? clock64() : 0;
       uint64_t twait = 0;
       const uint32_t q = p.limb[l].q, h = p.limb[l].h;
-      const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox);
-      uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
-      // Lane = (k octet j, row parity rp, slot half sh): a warp's 16-byte box
-      // reads at step kk cover all 8 bank groups (4 wavefronts per 512 B, the
-      // minimum) because the thread reads k offset kk ^ (j & 1) and slot half
-      // sh = s4 ^ ((j >> 1) & 1); the byte selectors of the plane transpose
-      // undo the swap of k offsets in odd octets.
-      const int j = lane >> 2, rp = (lane >> 1) & 1;
-      const int j0 = j & 1, sh = (lane & 1) ^ ((j >> 1) & 1);
-      const uint32_t sel_a = j0 ? 0x1504u : 0x5140u, sel_b = j0 ? 0x3726u : 0x7362u;
+      uint64_t cn = kNoUnit;
       bool got_all = true;
 #pragma unroll 1
-      for (int part = 0; part < T_TASK_CLIENTS / Cfg::BOX_CLIENTS; ++part) {
-        if (part > 0) asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");   // box buffer read out
+      for (int part = 0; part < NPART; ++part, ++gbox) {
         if (it == 0) {
-          const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
-          mbar_arrive_expect_tx(box_bar, Cfg::RAW_BOX);
-          if (p.hints)
-            tma_load_5d_hint(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0,
-                             l2_policy_evict_first());
-          else
-            tma_load_5d(rawbox, &p.ct_map, box_bar, (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0);
-          issued = true;
+          // the other buffer was read out before the last barrier
+          if (part + 1 < NPART) {
+            issue(gbox + 1, c, part + 1);
+          } else {
+            cn = claim_task();
+            if (cn != kNoUnit) issue(gbox + 1, cn, 0);
+          }
         }
+        const uint32_t b = gbox & 1u;
         const uint64_t tw0 = PROF ? clock64() : 0;
-        uint32_t got = wait(box_bar, rph, kErrTmaWait) ? 1u : 0u;
+        uint32_t got = wait(&box_bar[b], (gbox >> 1) & 1u, kErrTmaWait) ? 1u : 0u;
         if (PROF && it == 0) twait += clock64() - tw0;
         asm volatile(
             "{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
@@ -994,8 +1020,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           got_all = false;
           break;
         }
-        rph ^= 1u;
-        if (it == 0) issued = false;
+        if (it == 0) pend &= ~(1u << b);
+        const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox + b * Cfg::RAW_BOX);
 #pragma unroll 1
         for (int cb = it >> 5; cb < Cfg::BOX_CLIENTS; cb += NT / 32) {
           const int m_local = (part * Cfg::BOX_CLIENTS + cb) * 2 + rp;
@@ -1027,6 +1053,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
             }
           }
         }
+        asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");   // box buffer b read out
       }
       if (!got_all) break;
       if (PROF && it == 0) pc[PROF ? kTIWaitBox : 0] += twait;
@@ -1038,9 +1065,15 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         __threadfence();
         atomicAdd(&p.ready[E % p.R], 1u);
         if (PROF) pc[PROF ? kTIFence : 0] += clock64() - tfence;
+        *task_slot = cn;
       }
+      asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+      c = *task_slot;
     }
-    if (it == 0 && issued) mbar_wait_bounded(box_bar, rph, nullptr, 0);
+    // let box loads still in flight land before the CTA leaves
+    if (it == 0)
+      for (uint32_t b = 0; b < 2; ++b)
+        if ((pend >> b) & 1u) mbar_wait_bounded(&box_bar[b], (pend_ph >> b) & 1u, nullptr, 0);
   }
 #undef TM_TIMED
   if (PROF) {
