@@ -256,11 +256,14 @@ int gpir_fill_uniform(uint32_t *dst_dev, uint64_t count, uint64_t start, uint64_
 int gpir_rowsel_batch_noalloc(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev,
                               uint32_t *out_dev, void *stream);
 
-/* Tracing (the paper reports per-kernel device times, Sec. 5.1.2): when
- * enabled, each kernel the library launches is bracketed by CUDA events on
- * its launch stream. gpir_trace_read waits for the recorded launches, copies
- * up to max_records (name, milliseconds) pairs in launch order, sets *count,
- * and clears the log. Off by default; a disabled trace costs nothing. */
+/* Tracing (the paper reports per-kernel device times, Sec. 5.1.2): with
+ * on = 1, each kernel the library launches is bracketed by CUDA events on its
+ * launch stream; on = 2 also runs the tensor-core kernels' role-counting
+ * instantiations (slower: for gpir_trace_counters); on = 0 turns tracing off
+ * (the default; a disabled trace costs nothing); other values are
+ * GPIR_EINVAL. gpir_trace_read waits for the recorded launches, copies up to
+ * max_records (name, milliseconds) pairs in launch order, sets *count, and
+ * clears the log. */
 typedef struct gpir_trace_record {
   char name[32];
   float ms;
@@ -268,15 +271,16 @@ typedef struct gpir_trace_record {
 int gpir_trace_enable(int on);
 int gpir_trace_read(gpir_trace_record_t *out, uint32_t max_records, uint32_t *count);
 /* Wait-cycle counters of the last fused or cluster tensor-core launch made
- * while tracing was on (SM clock cycles summed over CTAs, one counting thread
+ * while tracing was at level 2 (SM clock cycles summed over CTAs, one counting thread
  * per role): [0] producer waiting for ingested tiles, [1] producer waiting for
  * a free stage, [2] MMA waiting for operands, [3] MMA waiting for the
  * epilogue, [4] epilogue waiting for MMAs, [5] epilogue waiting for the store
  * warp, [6] ingest waiting for a ring entry (cluster kernel: for a free stage),
  * [7] ingest waiting for its TMA box, [8] ingest converting, [9] cluster
  * ingest waiting for its slab copies to leave staging, [10] cluster ingest
- * issuing slab copies, [11] kernel cycles per CTA. Tracing makes that launch
- * synchronous. */
+ * issuing slab copies, [11] kernel cycles per CTA; the tensor-memory
+ * kernel's counters are listed with its binding. Tracing at level 2 makes that
+ * launch synchronous. */
 int gpir_trace_counters(unsigned long long *out, uint32_t max_counters, uint32_t *count);
 
 /* ColTor, the column tournament after RowSel (Sec. 2.2, "ColTor"), with the

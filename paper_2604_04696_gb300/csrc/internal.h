@@ -118,6 +118,7 @@ int rowsel_tc_default_variant(uint32_t batch, uint32_t d0, uint32_t d1);
 int trace_begin(const char *name, cudaStream_t s);
 void trace_end(int id, cudaStream_t s);
 bool trace_enabled();
+bool trace_counters_enabled();   // tracing at level 2: the role-counting kernel instantiations
 void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 
 // Tensor-memory kernel (rowsel_tmem.cu): its database layout, built at upload,

@@ -2054,7 +2054,7 @@ int tc_launch_fused(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint3
   fp.ctr = reinterpret_cast<unsigned long long *>(flags);
   fp.ready = reinterpret_cast<uint32_t *>(flags + 16);
   fp.consumed = fp.ready + R;
-  fp.prof = trace_enabled() ? reinterpret_cast<unsigned long long *>(fp.consumed + R) : nullptr;
+  fp.prof = trace_counters_enabled() ? reinterpret_cast<unsigned long long *>(fp.consumed + R) : nullptr;
   if (fp.prof && ((uintptr_t)fp.prof & 7)) fp.prof = reinterpret_cast<unsigned long long *>(((uintptr_t)fp.prof + 7) & ~(uintptr_t)7);
   e = cudaMemsetAsync(flags, 0, flag_bytes, stream);
   if (e != cudaSuccess) return set_cuda_error(e);
@@ -2169,7 +2169,7 @@ int tc_launch_cluster(const gpir_db *db, uint32_t batch, const uint32_t *ct, uin
     if (rc != GPIR_OK) return rc;
   }
   uint8_t *ws = nullptr;
-  if (trace_enabled()) {
+  if (trace_counters_enabled()) {
     const int rc = stream_workspace(stream, 8 * kNumFusedCounters, &ws);
     if (rc != GPIR_OK) return rc;
     e = cudaMemsetAsync(ws, 0, 8 * kNumFusedCounters, stream);

@@ -1244,7 +1244,7 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
   tp.ctr = reinterpret_cast<unsigned long long *>(flags);
   tp.ready = reinterpret_cast<uint32_t *>(flags + 16);
   tp.consumed = tp.ready + R;
-  tp.prof = trace_enabled()
+  tp.prof = trace_counters_enabled()
                 ? reinterpret_cast<unsigned long long *>(((uintptr_t)(tp.consumed + R) + 7) & ~(uintptr_t)7)
                 : nullptr;
   e = cudaMemsetAsync(flags, 0, flag_bytes, stream);

@@ -20,6 +20,7 @@ struct Rec {
 
 std::mutex g_mu;
 bool g_on = false;
+bool g_count_roles = false;   // tracing level 2
 std::vector<Rec> g_recs;
 std::vector<unsigned long long> g_counters;   // last kernel's wait-cycle counters
 
@@ -28,6 +29,11 @@ std::vector<unsigned long long> g_counters;   // last kernel's wait-cycle counte
 bool trace_enabled() {
   std::lock_guard<std::mutex> lk(g_mu);
   return g_on;
+}
+
+bool trace_counters_enabled() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on && g_count_roles;
 }
 
 // Copy a kernel's device counters to the host (synchronizes `s`).
@@ -67,8 +73,10 @@ void trace_end(int id, cudaStream_t s) {
 extern "C" {
 
 int gpir_trace_enable(int on) {
+  if (on < 0 || on > 2) return GPIR_EINVAL;
   std::lock_guard<std::mutex> lk(gpir::g_mu);
   gpir::g_on = on != 0;
+  gpir::g_count_roles = on == 2;
   return GPIR_OK;
 }
 

@@ -283,8 +283,10 @@ def gpir_fill_uniform(dst_dev, count, start, seed, tag, params, inner, stream=No
                                         int(inner), _stream(stream)), "gpir_fill_uniform")
 
 
-def gpir_trace_enable(on=True):
-    return _check(lib.gpir_trace_enable(1 if on else 0), "gpir_trace_enable")
+def gpir_trace_enable(on=True, counters=False):
+    """on: per-launch CUDA-event times; counters: also the role-counting
+    kernel instantiations (level 2, slower)."""
+    return _check(lib.gpir_trace_enable((2 if counters else 1) if on else 0), "gpir_trace_enable")
 
 
 def gpir_trace_read(max_records=4096):
