@@ -131,10 +131,12 @@ int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *
 
 /* Several RowSel problems at once (Sec. 5.1.1's batched GEMMs over a list of
  * jobs): different databases, uneven D0 / D1 and batch sizes. On the
- * tensor-core path the work units of up to 8 jobs are numbered into one
- * index space and processed by ONE persistent launch (one CTA per SM, units
- * taken round-robin by CTA index), after one ingest launch; larger lists use
- * one such pair per 8 jobs. CUDA-core and IMMA paths use one launch per job.
+ * tensor-core path one job runs the kernel tuned for its batch; the entries,
+ * work units and ingest tasks of up to 8 jobs are numbered into one index
+ * space and processed by ONE persistent launch of the tensor-memory kernel
+ * (one CTA per SM, work claimed in index order); larger lists use one launch
+ * per 8 jobs (databases uploaded without that kernel's digit tiles: the
+ * two-pass kernels). CUDA-core and IMMA paths use one launch per job.
  * GPIR_PATH_AUTO picks the tensor-core path when every job's database has
  * it. All jobs must share the same params (N, L, primes) and every job's
  * ct / out must not overlap any other buffer of the call. The tensor-core

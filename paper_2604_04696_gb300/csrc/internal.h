@@ -124,6 +124,8 @@ void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 // Tensor-memory kernel (rowsel_tmem.cu): its database layout, built at upload,
 // and one launch (pair: the SM-pair form; GPIR_ENOTSUP if it does not apply).
 int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream);
+// several RowSel jobs (one parameter set) in tensor-memory kernel launches of up to 8 jobs each
+int rowsel_tmem_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
 int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
                    uint32_t lookahead_mb, uint32_t hints, bool pair, cudaStream_t stream);
 // The tensor-core workspace kept for (current device, stream), grown on demand

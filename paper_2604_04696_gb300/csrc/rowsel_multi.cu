@@ -3,8 +3,9 @@
 // job list), and CUDA-graph plans of such calls.
 //
 // Tensor-core path: one job runs the kernel tuned for its batch; several jobs
-// have their work units numbered into one index space and processed by ONE
-// persistent GEMM launch (after one ingest launch), up to 8 jobs per launch.
+// have their entries, work units and ingest tasks numbered into one index
+// space and run in ONE persistent launch of the tensor-memory kernel, up to 8
+// jobs per launch.
 // CUDA-core and IMMA paths: one launch per job.
 #include <cuda_runtime.h>
 #include <string.h>
@@ -30,7 +31,13 @@ int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaSt
   if (p == GPIR_PATH_TC && njobs == 1)
     return dispatch(jobs[0].db, jobs[0].batch, jobs[0].ct, jobs[0].out, p, pick_variant(jobs[0].db, jobs[0].batch, p),
                     stream);
-  if (p == GPIR_PATH_TC) return rowsel_tc_multi(jobs, njobs, stream);
+  if (p == GPIR_PATH_TC) {
+    // several jobs: one persistent tensor-memory launch per 8 jobs; databases
+    // uploaded without its digit tiles fall back to the two-pass kernels
+    bool tmem = true;
+    for (uint32_t k = 0; k < njobs; ++k) tmem = tmem && jobs[k].db->db_digits12 != nullptr;
+    return tmem ? rowsel_tmem_multi(jobs, njobs, stream) : rowsel_tc_multi(jobs, njobs, stream);
+  }
   for (uint32_t k = 0; k < njobs; ++k) {
     int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, p,
                       pick_variant(jobs[k].db, jobs[k].batch, p), stream);

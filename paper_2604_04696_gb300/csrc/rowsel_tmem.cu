@@ -128,21 +128,55 @@ struct TmLimb {
   int32_t w[4][3];       // 2^(7u + 10v) mod q
 };
 
-struct TmemParams {
-  uint32_t L, N, M, d0, d1, mblk, nblk, kch;
-  uint32_t R, gpl, spg, lookahead;
-  uint32_t hints;                       // 1: raw boxes evict-first, ring stores evict-last in L2
-  uint64_t n_entries, upe, n_units, n_tasks;
+// One RowSel problem of a launch. Its entries, units and ingest tasks are
+// numbered after those of the jobs before it, in one index space per launch.
+constexpr int T_MAX_JOBS = 8;
+struct TmJob {
+  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, BOX_CLIENTS clients)
+  uint32_t M, d1, mblk, nblk, kch, upe;
+  uint64_t entry0, unit0, task0;        // first entry / unit / ingest task of the job
   const uint16_t *b_tiles;              // [slot][nblk][kch] x 24 KB
   uint32_t *out;
-  uint8_t *ring;                        // [R][8 slots][kch] x 8 KB
-  uint32_t *ready, *consumed;           // [R] each
+};
+
+struct TmemParams {
+  TmJob job[T_MAX_JOBS];
+  uint32_t L, N, njobs, kch_max;
+  uint32_t R, gpl, spg, lookahead;
+  uint32_t hints;                       // 1: raw boxes evict-first, ring stores evict-last in L2
+  uint64_t n_entries, n_units, n_tasks; // over all jobs
+  uint8_t *ring;                        // [R][8 slots][kch_max] x 8 KB
+  uint32_t *ready, *consumed;           // [n_entries] each: tasks ingested, units that read the entry
   unsigned long long *ctr;              // [0] next unit, [1] next ingest task
   unsigned int *err;
   unsigned long long *prof;             // wait-cycle counters (traced instantiation only)
-  CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, BOX_CLIENTS clients)
   TmLimb limb[GPIR_MAX_LIMBS];
 };
+
+// Job of a global unit / entry / ingest task (jobs in index order, at most
+// 8); job 0 at compile time in the single-job instantiations.
+template <bool MULTI>
+__device__ __forceinline__ uint32_t job_of_unit(const TmemParams &p, uint64_t u) {
+  uint32_t j = 0;
+  if constexpr (MULTI)
+    while (j + 1 < p.njobs && u >= p.job[j + 1].unit0) ++j;
+  return j;
+}
+template <bool MULTI>
+__device__ __forceinline__ uint32_t job_of_entry(const TmemParams &p, uint64_t e) {
+  uint32_t j = 0;
+  if constexpr (MULTI)
+    while (j + 1 < p.njobs && e >= p.job[j + 1].entry0) ++j;
+  return j;
+}
+template <bool MULTI>
+__device__ __forceinline__ uint32_t job_of_task(const TmemParams &p, uint64_t t) {
+  uint32_t j = 0;
+  if constexpr (MULTI)
+    while (j + 1 < p.njobs && t >= p.job[j + 1].task0) ++j;
+  return j;
+}
+
 
 // Wait / busy cycle counters of the traced instantiation (SM clock cycles
 // summed over CTAs, one counting thread per role), read through
@@ -312,17 +346,21 @@ __global__ void tm_pack_db_kernel(const Pack12Params p, uint64_t total) {
 // ---- the persistent kernel -------------------------------------------------
 //
 // Work: entries E = (8-slot group g, 32-row m-block), units (E, slot, n-block)
-// of kch k-chunks, ingest tasks (E, k-chunk). Claiming, ring flow control and
-// the deadlock argument are those of the fused kernel in rowsel_tc.cu (both
-// sides claim in increasing order; an ingest task waits only for the ring
-// entry R back and for claims already made); here the ring holds encoded raw
-// residues and the entry is released as soon as its unit's last k-chunk has
-// landed in shared memory. SM-pair form (PAIR): a pair unit covers entries
-// 2 E2 (even CTA) and 2 E2 + 1 (odd CTA) against one database tile; each CTA
-// copies its own ring tile and its half of B and converts its own A into its
-// own tensor memory; the even CTA's MMA thread issues M = 256 MMAs once both
-// CTAs' A buffers are ready; commits go to both CTAs.
-template <bool PROF, bool PAIR>
+// of kch k-chunks, ingest tasks (E, k-chunk), numbered job after job (MULTI:
+// several jobs, each with its own shape, database tiles, output and tensor
+// map; one parameter set). Claiming, ring flow control and the deadlock
+// argument are those of the fused kernel in rowsel_tc.cu (both sides claim in
+// increasing order; an ingest task waits only for the entry R back in the
+// ring and for claims already made), with one ready and one consumed counter
+// per entry (entries of different jobs need different counts); ring entries
+// are strided by the largest job's k-chunk count. The ring holds encoded raw
+// residues and an entry is released as soon as its units' last k-chunks have
+// landed in shared memory. SM-pair form (PAIR, one job): a pair unit covers
+// entries 2 E2 (even CTA) and 2 E2 + 1 (odd CTA) against one database tile;
+// each CTA copies its own ring tile and its half of B and converts its own A
+// into its own tensor memory; the even CTA's MMA thread issues M = 256 MMAs
+// once both CTAs' A buffers are ready; commits go to both CTAs.
+template <bool PROF, bool PAIR, bool MULTI>
 __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_constant__ TmemParams p) {
   using Cfg = TmemCfg<PAIR>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -473,7 +511,17 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     }
   };
   // entry of a unit for this CTA
-  auto entry_of = [&](uint64_t u) -> uint64_t { return PAIR ? (u / p.upe) * 2 + rank : u / p.upe; };
+  // global entry of a unit for this CTA
+  auto entry_of = [&](uint64_t u) -> uint64_t {
+    const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
+    const uint64_t ul = u - jb.unit0;
+    return jb.entry0 + (PAIR ? (ul / jb.upe) * 2 + rank : ul / jb.upe);
+  };
+  // index of the first unit that reads entry e
+  auto first_unit_of = [&](uint64_t e) -> uint64_t {
+    const TmJob &jb = p.job[job_of_entry<MULTI>(p, e)];
+    return jb.unit0 + ((e - jb.entry0) >> (PAIR ? 1 : 0)) * jb.upe;
+  };
   uint64_t pc[PROF ? kNumTmemCounters : 1];
 #pragma unroll
   for (int i = 0; i < (PROF ? kNumTmemCounters : 1); ++i) pc[i] = 0;
@@ -533,17 +581,18 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       ok = claim(u);
       if (ok && u != kNoUnit) ok = claim(un);
       while (ok && u != kNoUnit) {
+        const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
         const uint64_t E = entry_of(u);
-        const uint32_t w = (uint32_t)(u % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-        const uint32_t g = (uint32_t)(E / p.mblk);
+        const uint32_t w = (uint32_t)((u - jb.unit0) % jb.upe), sl = w / jb.nblk, nb = w % jb.nblk;
+        const uint32_t g = (uint32_t)((E - jb.entry0) / jb.mblk);
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        const uint8_t *src_a = p.ring + (((E % p.R) * 8 + sl) * p.kch) * (uint64_t)T_RAW_TILE;
-        const uint8_t *src_b = (const uint8_t *)p.b_tiles + ((slot * p.nblk + nb) * p.kch) * (uint64_t)T_B_TILE +
+        const uint8_t *src_a = p.ring + (((E % p.R) * 8 + sl) * p.kch_max) * (uint64_t)T_RAW_TILE;
+        const uint8_t *src_b = (const uint8_t *)jb.b_tiles + ((slot * jb.nblk + nb) * jb.kch) * (uint64_t)T_B_TILE +
                                (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
-        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[E % p.R], (uint32_t)((E / p.R + 1) * p.kch)))))
-          break;
+        const uint32_t kch = jb.kch;
+        if (!(ok = TM_TIMED(kTPWaitReady, wait_count(&p.ready[E], kch)))) break;
         fence_proxy_async_global();
-        for (uint32_t kc = 0; kc < p.kch; ++kc) {
+        for (uint32_t kc = 0; kc < kch; ++kc) {
           if (!(ok = TM_TIMED(kTPWaitEmpty, wait(&rempty[r], rph ^ 1u, kErrTmaWait)))) break;
           slot_unit[r] = u;
           slot_kc[r] = kc;
@@ -633,7 +682,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         break;
       }
       // the unit's last ring tile is in shared memory: its ring entry may be reused
-      if (qw == 0 && lane == 0 && slot_kc[r] + 1 == p.kch) atomicAdd(&p.consumed[entry_of(un) % p.R], 1u);
+      if (qw == 0 && lane == 0 && slot_kc[r] + 1 == p.job[job_of_unit<MULTI>(p, un)].kch)
+        atomicAdd(&p.consumed[entry_of(un)], 1u);
       // this thread's digit plane: 8 bytes per k octet (conflict-free: the
       // warp's 32 reads of a step cover every bank twice)
       const uint2 *row = reinterpret_cast<const uint2 *>(rslots + r * T_RAW_TILE) + m * 32;
@@ -680,7 +730,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       uint32_t st = 0, ph = 0, buf = 0, i = 0;
       uint32_t aph[2] = {0, 0};
       bool ok = true;
-      const uint32_t kgroups = (p.kch + T_KGROUP - 1) / T_KGROUP;
       auto wait_a = [&]() -> bool {
         if (i % Cfg::KPB) return true;
         const uint32_t bi = i / Cfg::KPB;
@@ -703,12 +752,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           break;
         }
         bool first = true;
+        const uint32_t kch = p.job[job_of_unit<MULTI>(p, u)].kch;
+        const uint32_t kgroups = (kch + T_KGROUP - 1) / T_KGROUP;
         for (uint32_t gi = 0; gi < kgroups && ok; ++gi) {
           if (!(ok = TM_TIMED(kTMWaitAcc, wait(&acc_empty[buf], aph[buf] ^ 1u, kErrMmaWait)))) break;
           tc_fence_after();
           const uint32_t tmem_d = tmem_base + buf * T_ACC_COLS;
           const uint32_t c0 = gi * T_KGROUP;
-          const uint32_t c1 = min(p.kch, c0 + T_KGROUP);
+          const uint32_t c1 = min(kch, c0 + T_KGROUP);
           for (uint32_t kc = c0; kc < c1; ++kc) {
             if (!first && !(ok = wait_a())) break;
             first = false;
@@ -807,8 +858,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       }
       const uint64_t un = tag & ~(1ull << 63);
       const bool last = (tag >> 63) != 0;
-      const uint64_t E = entry_of(un);
-      const uint32_t l = (uint32_t)(E / p.mblk) / p.gpl;
+      const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
+      const uint32_t l = (uint32_t)((entry_of(un) - jb.entry0) / jb.mblk) / p.gpl;
       const TmLimb &lm = p.limb[l];
       const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
       const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
@@ -899,17 +950,18 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       if (!__all_sync(0xffffffffu, wait(ostage_full, ph, kErrMmaWait))) break;
       const uint64_t un = *ostage_unit;
       if (un == kNoUnit) break;
-      const uint64_t E = entry_of(un);
-      const uint32_t w = (uint32_t)(un % p.upe), sl = w / p.nblk, nb = w % p.nblk;
-      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
+      const uint64_t El = entry_of(un) - jb.entry0;
+      const uint32_t w = (uint32_t)((un - jb.unit0) % jb.upe), sl = w / jb.nblk, nb = w % jb.nblk;
+      const uint32_t g = (uint32_t)(El / jb.mblk), mb = (uint32_t)(El % jb.mblk);
       const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
-      const uint32_t mrows = min((uint32_t)T_MROWS, p.M - mb * T_MROWS);
-      const uint32_t ncols = min((uint32_t)T_NCOLS, p.d1 - nb * T_NCOLS);
+      const uint32_t mrows = min((uint32_t)T_MROWS, jb.M - mb * T_MROWS);
+      const uint32_t ncols = min((uint32_t)T_NCOLS, jb.d1 - nb * T_NCOLS);
       const uint64_t nstride = (uint64_t)2 * p.L * p.N;
       for (uint32_t mm = 0; mm < mrows; ++mm) {
         const uint32_t mg = mb * T_MROWS + mm, c = mg >> 1, rr = mg & 1;
         const uint32_t sw = (mm & 7u) << 2;
-        uint32_t *orow = p.out + (((uint64_t)c * p.d1 + nb * T_NCOLS) * 2 + rr) * p.L * p.N + (uint64_t)l * p.N + t;
+        uint32_t *orow = jb.out + (((uint64_t)c * jb.d1 + nb * T_NCOLS) * 2 + rr) * p.L * p.N + (uint64_t)l * p.N + t;
 #pragma unroll
         for (uint32_t hh = 0; hh < T_NCOLS / 32; ++hh) {
           const uint32_t n = hh * 32 + lane;
@@ -939,19 +991,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     uint32_t pend = 0, pend_ph = 0;   // thread 0: box buffers loading, parity of their phase
     auto issue = [&](uint32_t gb, uint64_t task, int part) {
       // box gb (global box index) of `task`, part `part`, into buffer gb % 2
-      const uint64_t E = task / p.kch;
-      const uint32_t kc = (uint32_t)(task % p.kch);
-      const uint32_t g = (uint32_t)(E / p.mblk), mb = (uint32_t)(E % p.mblk);
+      const TmJob &jb = p.job[job_of_task<MULTI>(p, task)];
+      const uint64_t tl = task - jb.task0, El = tl / jb.kch;
+      const uint32_t kc = (uint32_t)(tl % jb.kch);
+      const uint32_t g = (uint32_t)(El / jb.mblk), mb = (uint32_t)(El % jb.mblk);
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       const uint32_t b = gb & 1u;
       const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
       uint8_t *dst = rawbox + b * Cfg::RAW_BOX;
       mbar_arrive_expect_tx(&box_bar[b], Cfg::RAW_BOX);
       if (p.hints)
-        tma_load_5d_hint(dst, &p.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0,
+        tma_load_5d_hint(dst, &jb.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0,
                          l2_policy_evict_first());
       else
-        tma_load_5d(dst, &p.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0);
+        tma_load_5d(dst, &jb.ct_map, &box_bar[b], (int)t0, (int)l, 0, (int)(kc * T_KCHUNK), c0);
       pend |= 1u << b;
       pend_ph = (pend_ph & ~(1u << b)) | (((gb >> 1) & 1u) << b);
     };
@@ -977,15 +1030,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     const uint32_t sel_a = j0 ? 0x1504u : 0x5140u, sel_b = j0 ? 0x3726u : 0x7362u;
     uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
     while (c != kNoUnit) {
-      const uint64_t E = c / p.kch;
-      const uint32_t kc = (uint32_t)(c % p.kch);
-      const uint32_t g = (uint32_t)(E / p.mblk);
+      const TmJob &jb = p.job[job_of_task<MULTI>(p, c)];
+      const uint64_t tl = c - jb.task0, El = tl / jb.kch;
+      const uint64_t E = jb.entry0 + El;   // global entry
+      const uint32_t kc = (uint32_t)(tl % jb.kch);
+      const uint32_t g = (uint32_t)(El / jb.mblk);
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       if (it == 0) {
+        // ring slot E % R: its previous entry E - R read by all of its units;
+        // and at most `lookahead` entries ahead of the units claimed
         const bool near = p.lookahead == 0 || E < p.lookahead ||
-                          TM_TIMED(kTIWaitSlot, wait_claims(((E - p.lookahead) >> (PAIR ? 1 : 0)) * p.upe));
-        const bool free = near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E % p.R],
-                                                                                (uint32_t)((E / p.R) * p.upe))));
+                          TM_TIMED(kTIWaitSlot, wait_claims(first_unit_of(E - p.lookahead)));
+        const bool free =
+            near && (E < p.R || TM_TIMED(kTIWaitSlot, wait_count(&p.consumed[E - p.R],
+                                                                 p.job[job_of_entry<MULTI>(p, E - p.R)].upe)));
         *task_ok = free ? 1u : 0u;   // task_slot may still be read for this task
       }
       asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
@@ -1038,7 +1096,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           for (int i = 0; i < 4; ++i) {
             const int sl = sh * 4 + i;
             if (t0 + sl >= p.N) continue;
-            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch + kc) * (uint64_t)T_RAW_TILE) / 16;
+            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
             uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
             digit_planes(z[0][i], z[1][i], z[2][i], z[3][i], sel_a, sel_b, pl);
             digit_planes(z[4][i], z[5][i], z[6][i], z[7][i], sel_a, sel_b, ph);
@@ -1063,7 +1121,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
       if (it == 0) {
         __threadfence();
-        atomicAdd(&p.ready[E % p.R], 1u);
+        atomicAdd(&p.ready[E], 1u);
         if (PROF) pc[PROF ? kTIFence : 0] += clock64() - tfence;
         *task_slot = cn;
       }
@@ -1169,38 +1227,47 @@ int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream) {
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
 }
 
-// One RowSel problem through the tensor-memory kernel. pair: the SM-pair
-// form; GPIR_ENOTSUP when the batch has an odd number of 32-row m-blocks or no
-// CTA pair can be resident.
-int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
-                   uint32_t lookahead_mb, uint32_t hints, bool pair, cudaStream_t stream) {
-  if (!db->db_digits12) return GPIR_ENOTSUP;
+// RowSel problems (at most T_MAX_JOBS, one parameter set) through one launch
+// of the tensor-memory kernel. pair: the SM-pair form; GPIR_ENOTSUP when a
+// job has an odd number of 32-row m-blocks or no CTA pair can be resident.
+int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_target, uint32_t lookahead_mb,
+                        uint32_t hints, bool pair, cudaStream_t stream) {
+  if (njobs == 0 || njobs > (uint32_t)T_MAX_JOBS) return GPIR_EINVAL;
+  if (pair && njobs > 1) return GPIR_ENOTSUP;   // the SM-pair form runs one job
+  for (uint32_t k = 0; k < njobs; ++k) {
+    if (!jobs[k].db->db_digits12) return GPIR_ENOTSUP;
+    const uint32_t mblk = (2 * jobs[k].batch + T_MROWS - 1) / T_MROWS;
+    if (pair && (mblk & 1u)) return GPIR_ENOTSUP;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e);
   if (dev < 0 || dev >= 64) return GPIR_EINVAL;
-  const uint32_t M = 2 * batch;
-  const uint32_t mblk = (M + T_MROWS - 1) / T_MROWS;
-  if (pair && (mblk & 1u)) return GPIR_ENOTSUP;
   {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     if (!g_tm_attr_done[dev]) {
-      e = cudaFuncSetAttribute(tc_tmem_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(tc_tmem_kernel<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)TmemCfg<false>::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_tmem_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_tmem_kernel<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TmemCfg<false>::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_tmem_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_tmem_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TmemCfg<false>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_tmem_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TmemCfg<false>::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_tmem_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TmemCfg<true>::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_tmem_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_tmem_kernel<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TmemCfg<true>::SMEM);
       if (e != cudaSuccess) return set_cuda_error(e);
       cudaLaunchAttribute attr[1];
       const cudaLaunchConfig_t cfg = tm_pair_config((unsigned)(sm_count() / 2 * 2), nullptr, attr);
       int n = 0;
-      e = cudaOccupancyMaxActiveClusters(&n, tc_tmem_kernel<false, true>, &cfg);
+      e = cudaOccupancyMaxActiveClusters(&n, tc_tmem_kernel<false, true, false>, &cfg);
       if (e != cudaSuccess) {
         cudaGetLastError();
         n = 0;
@@ -1210,32 +1277,57 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
     }
   }
   if (pair && g_tm_pairs[dev] < 0) return GPIR_ENOTSUP;
-  const gpir_params &prm = db->params;
+  const gpir_params &prm = jobs[0].db->params;
   const uint32_t L = prm.num_limbs, N = prm.n;
   TmemParams tp;
   memset(&tp, 0, sizeof(tp));
   tp.L = L;
   tp.N = N;
-  tp.M = M;
-  tp.d0 = db->d0;
-  tp.d1 = db->d1;
-  tp.mblk = mblk;
-  tp.nblk = (db->d1 + T_NCOLS - 1) / T_NCOLS;
-  tp.kch = (db->d0 + T_KCHUNK - 1) / T_KCHUNK;
+  tp.njobs = njobs;
   tp.gpl = (N + 7) / 8;
-  tp.n_entries = (uint64_t)tp.gpl * L * mblk;
   tp.spg = N < 8 ? N : 8u;
-  tp.upe = (uint64_t)tp.spg * tp.nblk;
-  tp.n_units = (pair ? tp.n_entries / 2 : tp.n_entries) * tp.upe;
-  tp.n_tasks = tp.n_entries * tp.kch;
-  const size_t entry_bytes = (size_t)8 * tp.kch * T_RAW_TILE;
+  uint64_t entries = 0, units = 0, tasks = 0;
+  uint32_t kch_max = 1;
+  for (uint32_t k = 0; k < njobs; ++k) {
+    const gpir_db *db = jobs[k].db;
+    TmJob &jb = tp.job[k];
+    jb.M = 2 * jobs[k].batch;
+    jb.d1 = db->d1;
+    jb.mblk = (jb.M + T_MROWS - 1) / T_MROWS;
+    jb.nblk = (db->d1 + T_NCOLS - 1) / T_NCOLS;
+    jb.kch = (db->d0 + T_KCHUNK - 1) / T_KCHUNK;
+    jb.upe = tp.spg * jb.nblk;
+    jb.entry0 = entries;
+    jb.unit0 = units;
+    jb.task0 = tasks;
+    jb.b_tiles = db->db_digits12;
+    jb.out = jobs[k].out;
+    const uint64_t ne = (uint64_t)tp.gpl * L * jb.mblk;
+    entries += ne;
+    units += (pair ? ne / 2 : ne) * jb.upe;
+    tasks += ne * jb.kch;
+    kch_max = std::max(kch_max, jb.kch);
+    const uint64_t dims[5] = {N, L, 2, db->d0, jobs[k].batch};
+    const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
+                             (uint64_t)db->d0 * 2 * L * N * 4};
+    const uint32_t box[5] = {8, 1, 2, (uint32_t)T_KCHUNK,
+                             (uint32_t)(pair ? TmemCfg<true>::BOX_CLIENTS : TmemCfg<false>::BOX_CLIENTS)};
+    const int rc = encode_tiled_u32(&jb.ct_map, jobs[k].ct, 5, dims, str, box);
+    if (rc != GPIR_OK) return rc;
+  }
+  tp.n_entries = entries;
+  tp.n_units = units;
+  tp.n_tasks = tasks;
+  tp.kch_max = kch_max;
+  const size_t entry_bytes = (size_t)8 * kch_max * T_RAW_TILE;
   uint64_t R = ring_target / entry_bytes;
   if (R < 2) R = 2;
   if (pair && (R & 1)) ++R;   // both entries of a pair unit share R's parity classes
   if (R > tp.n_entries) R = tp.n_entries;
   tp.R = (uint32_t)R;
   const size_t ring_bytes = (size_t)R * entry_bytes;
-  const size_t flag_bytes = ((size_t)8 * R + 16 + 8 + 8 * kNumTmemCounters + 255) & ~(size_t)255;
+  // counters: [2] claims, ready[n_entries], consumed[n_entries], role counters
+  const size_t flag_bytes = ((size_t)16 + 8 * entries + 8 + 8 * kNumTmemCounters + 255) & ~(size_t)255;
   uint8_t *ws = nullptr;
   int rc = tc_stream_workspace(stream, ring_bytes + flag_bytes, &ws);
   if (rc != GPIR_OK) return rc;
@@ -1243,23 +1335,12 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
   uint8_t *flags = ws + ring_bytes;
   tp.ctr = reinterpret_cast<unsigned long long *>(flags);
   tp.ready = reinterpret_cast<uint32_t *>(flags + 16);
-  tp.consumed = tp.ready + R;
+  tp.consumed = tp.ready + entries;
   tp.prof = trace_counters_enabled()
-                ? reinterpret_cast<unsigned long long *>(((uintptr_t)(tp.consumed + R) + 7) & ~(uintptr_t)7)
+                ? reinterpret_cast<unsigned long long *>(((uintptr_t)(tp.consumed + entries) + 7) & ~(uintptr_t)7)
                 : nullptr;
   e = cudaMemsetAsync(flags, 0, flag_bytes, stream);
   if (e != cudaSuccess) return set_cuda_error(e);
-  {
-    const uint64_t dims[5] = {N, L, 2, db->d0, batch};
-    const uint64_t str[4] = {(uint64_t)N * 4, (uint64_t)L * N * 4, (uint64_t)2 * L * N * 4,
-                             (uint64_t)db->d0 * 2 * L * N * 4};
-    const uint32_t box[5] = {8, 1, 2, (uint32_t)T_KCHUNK,
-                             (uint32_t)(pair ? TmemCfg<true>::BOX_CLIENTS : TmemCfg<false>::BOX_CLIENTS)};
-    rc = encode_tiled_u32(&tp.ct_map, ct, 5, dims, str, box);
-    if (rc != GPIR_OK) return rc;
-  }
-  tp.b_tiles = db->db_digits12;
-  tp.out = out;
   tp.hints = hints;
   tp.lookahead =
       lookahead_mb == 0 ? 0u : (uint32_t)std::max<uint64_t>(2, ((uint64_t)lookahead_mb << 20) / entry_bytes);
@@ -1269,8 +1350,8 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
     cudaLaunchAttribute attr[1];
     const cudaLaunchConfig_t cfg = tm_pair_config((unsigned)(2 * g_tm_pairs[dev]), stream, attr);
     const int tr = trace_begin("tc_tmem_pair", stream);
-    e = tp.prof ? cudaLaunchKernelEx(&cfg, tc_tmem_kernel<true, true>, tp)
-                : cudaLaunchKernelEx(&cfg, tc_tmem_kernel<false, true>, tp);
+    e = tp.prof ? cudaLaunchKernelEx(&cfg, tc_tmem_kernel<true, true, false>, tp)
+                : cudaLaunchKernelEx(&cfg, tc_tmem_kernel<false, true, false>, tp);
     trace_end(tr, stream);
     if (e != cudaSuccess) return set_cuda_error(e);
     if (tp.prof) trace_counters(tp.prof, kNumTmemCounters, stream);
@@ -1279,13 +1360,38 @@ int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32
   }
   const int tr = trace_begin("tc_tmem", stream);
   if (tp.prof)
-    tc_tmem_kernel<true, false><<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
+    (njobs > 1 ? tc_tmem_kernel<true, false, true> : tc_tmem_kernel<true, false, false>)
+        <<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
   else
-    tc_tmem_kernel<false, false><<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
+    (njobs > 1 ? tc_tmem_kernel<false, false, true> : tc_tmem_kernel<false, false, false>)
+        <<<sm_count(), T_THREADS, TmemCfg<false>::SMEM, stream>>>(tp);
   trace_end(tr, stream);
   if (tp.prof) trace_counters(tp.prof, kNumTmemCounters, stream);
   e = cudaGetLastError();
   return e == cudaSuccess ? GPIR_OK : set_cuda_error(e);
+}
+
+
+// Several jobs, T_MAX_JOBS per launch, in the single-CTA form with the ring
+// and lookahead of tile variant 8.
+int rowsel_tmem_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream) {
+  for (uint32_t k0 = 0; k0 < njobs; k0 += T_MAX_JOBS) {
+    const uint32_t n = std::min<uint32_t>(T_MAX_JOBS, njobs - k0);
+    const int rc = tc_launch_tmem_jobs(jobs + k0, n, (size_t)48 << 20, 16, 0, false, stream);
+    if (rc != GPIR_OK) return rc;
+  }
+  return GPIR_OK;
+}
+
+int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,
+                   uint32_t lookahead_mb, uint32_t hints, bool pair, cudaStream_t stream) {
+  gpir_job_t job;
+  memset(&job, 0, sizeof(job));
+  job.db = db;
+  job.batch = batch;
+  job.ct = ct;
+  job.out = out;
+  return tc_launch_tmem_jobs(&job, 1, ring_target, lookahead_mb, hints, pair, stream);
 }
 
 }  // namespace gpir

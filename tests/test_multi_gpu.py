@@ -168,3 +168,52 @@ def test_multi_argument_errors(g):
     finally:
         g.gpir_db_free(h)
         g.gpir_params_destroy(params)
+
+
+def test_multi_job_tensor_memory_launch_with_ring_wrap(g):
+    """Four uneven jobs at N = 512 (batches 17 / 33 / 8 / 25, D0 700 / 130 / 64 /
+    257, D1 130 / 40 / 64 / 1): one persistent tensor-memory launch, whose
+    48 MB ring of 704 KB entries (the largest job's 11 k-chunks: 69 entries)
+    wraps about 15 times over the jobs' 1024 entries. Every output equals the same job
+    through gpir_rowsel_batch on the tensor-core path, and the oracle on 16
+    spread slots of each job."""
+    import torch
+    from tests.gpu_util import to_host
+    if g.gpir_num_variants(g.GPIR_PATH_TC) == 0:
+        pytest.skip("tensor-core path not built")
+    N, L = 512, 2
+    primes = list(synth.PRIMES_28[:L])
+    shapes = [(17, 700, 130), (33, 130, 40), (8, 64, 64), (25, 257, 1)]
+    params = g.gpir_params_create(N, primes)
+    handles, jobs, outs, refs, data = [], [], [], [], []
+    try:
+        for k, (B, D0, D1) in enumerate(shapes):
+            db = torch.empty((D0, D1, L, N), dtype=torch.int32, device="cuda")
+            g.gpir_fill_uniform(db, db.numel(), 0, 40 + k, synth.TAG_DB, params, N)
+            h = g.gpir_db_upload(params, D0, D1, db, True, 0)
+            handles.append(h)
+            ct = torch.empty((B, D0, 2, L, N), dtype=torch.int32, device="cuda")
+            g.gpir_fill_uniform(ct, ct.numel(), 0, 40 + k, synth.TAG_CT, params, N)
+            out = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
+            ref = torch.full((B, D1, 2, L, N), -2, dtype=torch.int32, device="cuda")
+            g.gpir_rowsel_batch(h, B, ct, ref, g.GPIR_PATH_TC)
+            jobs.append((h, B, ct, out))
+            outs.append(out)
+            refs.append(ref)
+            data.append((db, ct))
+        g.gpir_rowsel_multi(jobs, g.GPIR_PATH_TC)
+        torch.cuda.synchronize()
+        g.gpir_sync(None, 30000)
+        for k, (B, D0, D1) in enumerate(shapes):
+            got = to_host(outs[k])
+            assert np.array_equal(got, to_host(refs[k])), "job %d differs from its single-job call" % k
+            db, ct = data[k]
+            for s in range(16):
+                l, t = s % L, (s * 67 + k * 5) % N
+                want = oracle.rowsel(to_host(ct[:, :, :, l:l + 1, t:t + 1].contiguous()),
+                                     to_host(db[:, :, l:l + 1, t:t + 1].contiguous()), [primes[l]])
+                assert np.array_equal(got[:, :, :, l:l + 1, t:t + 1], want), "job %d slot (%d, %d)" % (k, l, t)
+    finally:
+        for h in handles:
+            g.gpir_db_free(h)
+        g.gpir_params_destroy(params)
