@@ -1,5 +1,6 @@
 // RowSel on the tensor cores with the A operand in tensor memory and 12 digit
-// products per modular MAC (the tensor-memory kernel, tile variants 8 and 9).
+// products per modular MAC (the tensor-memory kernel: tile variants 8-11, and
+// the multi-job form of several RowSel problems in one launch).
 //
 // What is computed: the per-point modular GEMM of Sec. 2.3 / Sec. 5.1 of the
 // GPIR paper, out[p][m][n] = sum_k ct[p][m][k] * db[p][k][n] mod q, with
