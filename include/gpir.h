@@ -137,8 +137,10 @@ int gpir_rowsel_batch_host(const gpir_db_t *db, uint32_t batch, const uint32_t *
  * (one CTA per SM, work claimed in index order); larger lists use one launch
  * per 8 jobs (databases uploaded without that kernel's digit tiles: the
  * two-pass kernels). CUDA-core and IMMA paths use one launch per job.
- * GPIR_PATH_AUTO picks the tensor-core path when every job's database has
- * it. All jobs must share the same params (N, L, primes) and every job's
+ * GPIR_PATH_AUTO runs each job on the path gpir_rowsel_batch would choose for
+ * its batch (the autotuned one, else tensor cores from batch 8), the
+ * tensor-core jobs together. All jobs must share the same params (N, L,
+ * primes) and every job's
  * ct / out must not overlap any other buffer of the call. The tensor-core
  * workspace for the call is grown on demand (not while the stream is being
  * captured: GPIR_ENOMEM then); it is per (device, stream), so calls on

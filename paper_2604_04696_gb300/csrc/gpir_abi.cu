@@ -227,7 +227,7 @@ int pick_variant(const gpir_db *db, uint32_t batch, int path) {
 // GPIR_PATH_AUTO: the path the autotuner measured fastest for this batch size,
 // else a static choice: tensor cores once a batch fills a 32-row tile well
 // (batch >= 8), CUDA cores below that (one client wastes 15/16 of an MMA tile).
-static int resolve_path(const gpir_db *db, int path, uint32_t batch) {
+int resolve_path(const gpir_db *db, int path, uint32_t batch) {
   if (path == GPIR_PATH_AUTO) {
     {
       std::lock_guard<std::mutex> lk(*db->mu);

@@ -124,6 +124,9 @@ void trace_counters(const unsigned long long *dev, int n, cudaStream_t s);
 // Tensor-memory kernel (rowsel_tmem.cu): its database layout, built at upload,
 // and one launch (pair: the SM-pair form; GPIR_ENOTSUP if it does not apply).
 int rowsel_tmem_prepare(gpir_db *db, cudaStream_t stream);
+// the path gpir_rowsel_batch runs for (db, batch) under `path` (GPIR_PATH_AUTO:
+// the autotuned one, else tensor cores from batch 8, CUDA cores below); < 0: none
+int resolve_path(const gpir_db *db, int path, uint32_t batch);
 // several RowSel jobs (one parameter set) in tensor-memory kernel launches of up to 8 jobs each
 int rowsel_tmem_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream);
 int tc_launch_tmem(const gpir_db *db, uint32_t batch, const uint32_t *ct, uint32_t *out, size_t ring_target,

@@ -5,8 +5,8 @@
 // Tensor-core path: one job runs the kernel tuned for its batch; several jobs
 // have their entries, work units and ingest tasks numbered into one index
 // space and run in ONE persistent launch of the tensor-memory kernel, up to 8
-// jobs per launch.
-// CUDA-core and IMMA paths: one launch per job.
+// jobs per launch. CUDA-core and IMMA paths: one launch per job.
+// GPIR_PATH_AUTO: each job on the path gpir_rowsel_batch would choose for it.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -17,30 +17,42 @@
 
 namespace gpir {
 
+// Tensor-core jobs of one call: one job runs the kernel tuned for its batch;
+// several run in one persistent tensor-memory launch per 8 jobs (databases
+// uploaded without its digit tiles: the two-pass kernels).
+static int tc_jobs(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream) {
+  if (njobs == 1)
+    return dispatch(jobs[0].db, jobs[0].batch, jobs[0].ct, jobs[0].out, GPIR_PATH_TC,
+                    pick_variant(jobs[0].db, jobs[0].batch, GPIR_PATH_TC), stream);
+  bool tmem = true;
+  for (uint32_t k = 0; k < njobs; ++k) tmem = tmem && jobs[k].db->db_digits12 != nullptr;
+  return tmem ? rowsel_tmem_multi(jobs, njobs, stream) : rowsel_tc_multi(jobs, njobs, stream);
+}
+
 int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaStream_t stream) {
-  int p = path;
-  if (p == GPIR_PATH_AUTO) {
-    bool all_tc = true;
-    for (uint32_t k = 0; k < njobs; ++k) all_tc = all_tc && (jobs[k].db->path_mask & GPIR_PATH_TC);
-    p = all_tc ? GPIR_PATH_TC : GPIR_PATH_CUDACORE;
+  if (path == GPIR_PATH_AUTO) {
+    // each job on the path gpir_rowsel_batch would take for it (small batches
+    // on the CUDA cores); the tensor-core jobs together
+    std::vector<gpir_job_t> tc;
+    for (uint32_t k = 0; k < njobs; ++k) {
+      const int p = resolve_path(jobs[k].db, GPIR_PATH_AUTO, jobs[k].batch);
+      if (p < 0) return GPIR_ENOTSUP;
+      if (p == GPIR_PATH_TC) {
+        tc.push_back(jobs[k]);
+        continue;
+      }
+      const int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, p,
+                              pick_variant(jobs[k].db, jobs[k].batch, p), stream);
+      if (rc) return rc;
+    }
+    return tc.empty() ? GPIR_OK : tc_jobs(tc.data(), (uint32_t)tc.size(), stream);
   }
   for (uint32_t k = 0; k < njobs; ++k)
-    if (!(jobs[k].db->path_mask & p)) return GPIR_ENOTSUP;
-  // one job (a single database's batch, and every graph of one): the kernel
-  // tuned for that batch; several: all of them in one persistent launch pair
-  if (p == GPIR_PATH_TC && njobs == 1)
-    return dispatch(jobs[0].db, jobs[0].batch, jobs[0].ct, jobs[0].out, p, pick_variant(jobs[0].db, jobs[0].batch, p),
-                    stream);
-  if (p == GPIR_PATH_TC) {
-    // several jobs: one persistent tensor-memory launch per 8 jobs; databases
-    // uploaded without its digit tiles fall back to the two-pass kernels
-    bool tmem = true;
-    for (uint32_t k = 0; k < njobs; ++k) tmem = tmem && jobs[k].db->db_digits12 != nullptr;
-    return tmem ? rowsel_tmem_multi(jobs, njobs, stream) : rowsel_tc_multi(jobs, njobs, stream);
-  }
+    if (!(jobs[k].db->path_mask & path)) return GPIR_ENOTSUP;
+  if (path == GPIR_PATH_TC) return tc_jobs(jobs, njobs, stream);
   for (uint32_t k = 0; k < njobs; ++k) {
-    int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, p,
-                      pick_variant(jobs[k].db, jobs[k].batch, p), stream);
+    int rc = dispatch(jobs[k].db, jobs[k].batch, jobs[k].ct, jobs[k].out, path,
+                      pick_variant(jobs[k].db, jobs[k].batch, path), stream);
     if (rc) return rc;
   }
   return GPIR_OK;
