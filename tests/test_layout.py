@@ -11,13 +11,25 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = os.path.join(ROOT, "paper_2604_04696_gb300")
 
 
+def _ignored_dirs():
+    """Directory entries of .gitignore (lines ending in '/'), without slashes."""
+    try:
+        lines = open(os.path.join(ROOT, ".gitignore"), encoding="utf-8").read().splitlines()
+    except OSError:
+        return set()
+    return {ln.strip().strip("/") for ln in lines if ln.strip().endswith("/") and not ln.startswith("#")}
+
+
 def _committed_files():
     r = subprocess.run(["git", "ls-files"], cwd=ROOT, capture_output=True, text=True)
     if r.returncode != 0:
+        # no git metadata (a copy of the tree): everything but hidden and ignored directories
+        skip = _ignored_dirs()
         files = []
-        for d, _, fs in os.walk(ROOT):
-            if "/." in d or "/_work" in d or "gpurun_out" in d:
-                continue
+        for d, dirs, fs in os.walk(ROOT):
+            rel = os.path.relpath(d, ROOT)
+            dirs[:] = [x for x in dirs if not x.startswith(".") and x not in skip
+                       and os.path.join(rel, x).lstrip("./") not in skip]
             files += [os.path.relpath(os.path.join(d, f), ROOT) for f in fs]
         return files
     return [f for f in r.stdout.splitlines() if f]
