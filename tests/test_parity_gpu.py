@@ -127,6 +127,42 @@ def test_tmem_extreme_digits_reach_the_bound(g, B, xy):
         h.close()
 
 
+@pytest.mark.parametrize("B,D0", [(5, 2600), (34, 3100)])
+def test_tmem_deferred_reduction_across_flushes(g, B, D0):
+    """The tensor-memory epilogue sums four 512-row groups before one
+    reduction: D0 = 2600 (6 groups, the last partial) and 3100 (7 groups)
+    reduce once in the middle of each unit and once at its end. Random
+    residues, every tensor-memory variant, against the oracle; B = 34 gives
+    three 32-row m-blocks (the pair variants run pairs plus a single)."""
+    _check_full(g, B, D0, 70, 2, 16, synth.PRIMES_28, 3000 + D0, PATHS["tc"], variants=TMEM_VARIANTS)
+
+
+def test_tmem_extreme_digits_over_eight_groups(g):
+    """Bound-driving residues (ciphertext q - 1056832, database q - 524800: six
+    of the twelve group sums at exactly 2^24) over D0 = 4096 rows, eight
+    groups, two deferred reductions per unit: result D0 * x * y mod q."""
+    from tests.gpu_util import DbHandle, to_dev, to_host
+    _skip_unbuilt(g, PATHS["tc"])
+    primes = synth.PRIMES_28
+    B, D0, D1, L, N = 16, 4096, 70, 2, 16
+    ct = np.empty((B, D0, 2, L, N), dtype=np.uint32)
+    db = np.empty((D0, D1, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        ct[:, :, :, l] = q - 1056832
+        db[:, :, l] = q - 524800
+    h = DbHandle(g, db, N, primes, path_mask=PATHS["tc"])
+    try:
+        ct_d = to_dev(ct)
+        for v in TMEM_VARIANTS:
+            g.gpir_set_variant(h.h, B, PATHS["tc"], v)
+            got = to_host(h.rowsel(ct_d, B, PATHS["tc"]))
+            for l, q in enumerate(primes):
+                want = (D0 * (q - 1056832) * (q - 524800)) % q
+                assert np.all(got[:, :, :, l] == want), (v, l)
+    finally:
+        h.close()
+
+
 @pytest.mark.parametrize("path", PATH_LIST)
 def test_worst_case_accumulation(g, path):
     """All residues q-1 with D0 = 2048: every product is maximal; result D0 mod q."""
