@@ -171,10 +171,12 @@ def test_multi_argument_errors(g):
 
 
 def test_multi_job_tensor_memory_launch_with_ring_wrap(g):
-    """Four uneven jobs at N = 512 (batches 17 / 33 / 8 / 25, D0 700 / 130 / 64 /
-    257, D1 130 / 40 / 64 / 1): one persistent tensor-memory launch, whose
-    48 MB ring of 704 KB entries (the largest job's 11 k-chunks: 69 entries)
-    wraps about 15 times over the jobs' 1024 entries. Every output equals the same job
+    """Five uneven jobs at N = 512 (batches 17 / 33 / 8 / 25 / 3, D0 700 / 130 /
+    64 / 257 / 2600, D1 130 / 40 / 64 / 1 / 9): one persistent tensor-memory
+    launch, whose 48 MB ring of 2.6 MB entries (the largest job's 41 k-chunks:
+    18 entries) wraps 64 times over the jobs' 1152 entries; the last job
+    has six 512-row groups, so its epilogue reduces in the middle of each
+    unit. Every output equals the same job
     through gpir_rowsel_batch on the tensor-core path, and the oracle on 16
     spread slots of each job."""
     import torch
@@ -183,7 +185,7 @@ def test_multi_job_tensor_memory_launch_with_ring_wrap(g):
         pytest.skip("tensor-core path not built")
     N, L = 512, 2
     primes = list(synth.PRIMES_28[:L])
-    shapes = [(17, 700, 130), (33, 130, 40), (8, 64, 64), (25, 257, 1)]
+    shapes = [(17, 700, 130), (33, 130, 40), (8, 64, 64), (25, 257, 1), (3, 2600, 9)]
     params = g.gpir_params_create(N, primes)
     handles, jobs, outs, refs, data = [], [], [], [], []
     try:
