@@ -219,3 +219,39 @@ def test_multi_job_tensor_memory_launch_with_ring_wrap(g):
         for h in handles:
             g.gpir_db_free(h)
         g.gpir_params_destroy(params)
+
+
+def test_multi_job_same_database_twice(g):
+    """Two jobs on one database (different batches, ciphertexts and outputs)
+    and a third on another, in one tensor-memory launch, against the oracle."""
+    import torch
+    from tests.gpu_util import to_dev, to_host
+    if g.gpir_num_variants(g.GPIR_PATH_TC) == 0:
+        pytest.skip("tensor-core path not built")
+    N, L = 64, 2
+    primes = list(synth.PRIMES_28[:L])
+    params = g.gpir_params_create(N, primes)
+    dbA = synth.db_tensor(610, 150, 80, L, N, primes)
+    dbB = synth.db_tensor(611, 70, 20, L, N, primes)
+    hA = g.gpir_db_upload(params, 150, 80, to_dev(dbA), True, 0)
+    hB = g.gpir_db_upload(params, 70, 20, to_dev(dbB), True, 0)
+    try:
+        specs = [(hA, dbA, 20, 150, 80, 612), (hA, dbA, 9, 150, 80, 613), (hB, dbB, 12, 70, 20, 614)]
+        jobs, outs, wants, keep = [], [], [], []
+        for h, db, B, D0, D1, seed in specs:
+            ct = synth.ct_tensor(seed, B, D0, L, N, primes)
+            ctd = to_dev(ct)
+            out = torch.full((B, D1, 2, L, N), -1, dtype=torch.int32, device="cuda")
+            jobs.append((h, B, ctd, out))
+            keep.append(ctd)
+            outs.append(out)
+            wants.append(oracle.rowsel(ct, db, primes))
+        g.gpir_rowsel_multi(jobs, g.GPIR_PATH_TC)
+        torch.cuda.synchronize()
+        g.gpir_sync(None, 30000)
+        for k, (out, want) in enumerate(zip(outs, wants)):
+            assert np.array_equal(to_host(out), want), "job %d" % k
+    finally:
+        g.gpir_db_free(hA)
+        g.gpir_db_free(hB)
+        g.gpir_params_destroy(params)

@@ -92,6 +92,13 @@ def test_tmem_kernel_vs_oracle(g, shape):
     _check_full(g, B, D0, D1, L, N, primes, 2000 + B + D0, PATHS["tc"], variants=TMEM_VARIANTS)
 
 
+def test_tmem_kernel_many_clients(g):
+    """257 clients: 17 m-blocks of 32 rows, the last with 2 rows (the SM-pair
+    variants, which need an even count, run the single-CTA form), ragged D0
+    and D1, against the oracle."""
+    _check_full(g, 257, 100, 70, 2, 32, synth.PRIMES_28, 4257, PATHS["tc"], variants=TMEM_VARIANTS)
+
+
 @pytest.mark.parametrize("B", [16, 33])
 @pytest.mark.parametrize("xy", [("q-1056832", "q-524800"), ("133160903", "q-524800"), ("h", "h+1"),
                                 ("q-1", "q-1")])
