@@ -165,7 +165,11 @@ int check_residues_dev(const gpir_params &prm, const uint32_t *v, uint64_t count
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_range_flag);
     if (e != cudaSuccess) return set_cuda_error(e);
-    it = flags.emplace(dev, static_cast<unsigned int *>(p)).first;
+    try {
+      it = flags.emplace(dev, static_cast<unsigned int *>(p)).first;
+    } catch (...) {   // no exception crosses the C ABI
+      return GPIR_ENOMEM;
+    }
   }
   if (count == 0) return GPIR_OK;
   unsigned int *flag = it->second;
@@ -346,10 +350,15 @@ int gpir_db_upload(const gpir_params_t *params, uint32_t d0, uint32_t d1, const 
   db->d1 = d1;
   db->path_mask = path_mask;
   cudaGetDevice(&db->device);
-  db->variants = new std::map<std::pair<int, uint32_t>, int>();
-  db->mu = new std::mutex();
+  db->variants = new (std::nothrow) std::map<std::pair<int, uint32_t>, int>();
+  db->mu = new (std::nothrow) std::mutex();
   int rc = GPIR_OK;
-  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&db->db_pmajor), bytes);
+  cudaError_t e = cudaSuccess;
+  if (!db->variants || !db->mu) {
+    rc = GPIR_ENOMEM;
+    goto fail;
+  }
+  e = dev_malloc(reinterpret_cast<void **>(&db->db_pmajor), bytes);
   if (e != cudaSuccess) {
     db->db_pmajor = nullptr;
     rc = set_cuda_error(e);
@@ -461,9 +470,23 @@ int host_pipe(int dev, HostPipe **out) {
     e = cudaEventCreateWithFlags(&hp.copied[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.computed[k], cudaEventDisableTiming);
   }
-  if (e != cudaSuccess) return set_cuda_error(e);
-  *out = &g_pipes.emplace(dev, hp).first->second;
-  return GPIR_OK;
+  if (e == cudaSuccess) {
+    try {
+      *out = &g_pipes.emplace(dev, hp).first->second;
+      return GPIR_OK;
+    } catch (...) {   // no exception crosses the C ABI
+      e = cudaErrorMemoryAllocation;
+    }
+  }
+  if (hp.in) cudaStreamDestroy(hp.in);
+  if (hp.out) cudaStreamDestroy(hp.out);
+  if (hp.start) cudaEventDestroy(hp.start);
+  if (hp.done) cudaEventDestroy(hp.done);
+  for (int k = 0; k < HostPipe::kMaxChunks; ++k) {
+    if (hp.copied[k]) cudaEventDestroy(hp.copied[k]);
+    if (hp.computed[k]) cudaEventDestroy(hp.computed[k]);
+  }
+  return set_cuda_error(e);
 }
 }  // namespace
 
@@ -653,7 +676,11 @@ int gpir_selected_variant(const gpir_db_t *db, uint32_t batch, int path) {
 int gpir_set_variant(const gpir_db_t *db, uint32_t batch, int path, int variant) {
   if (!db || variant < 0 || variant >= num_variants(path)) return GPIR_EINVAL;
   std::lock_guard<std::mutex> lk(*db->mu);
-  (*db->variants)[{path, batch}] = variant;
+  try {
+    (*db->variants)[{path, batch}] = variant;
+  } catch (...) {   // no exception crosses the C ABI
+    return GPIR_ENOMEM;
+  }
   return GPIR_OK;
 }
 
@@ -708,7 +735,11 @@ int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, u
     }
     if (pv >= 0) {
       std::lock_guard<std::mutex> lk(*db->mu);
-      (*db->variants)[{p, batch}] = pv;
+      try {
+        (*db->variants)[{p, batch}] = pv;
+      } catch (...) {
+        return GPIR_ENOMEM;
+      }
     }
     if (pv >= 0 && pv_ms < best_ms) {
       best_ms = pv_ms;
@@ -721,7 +752,11 @@ int gpir_autotune(const gpir_db_t *db, uint32_t batch, const uint32_t *ct_dev, u
   if (best_path < 0) return GPIR_ENOTSUP;
   if (path == GPIR_PATH_AUTO) {
     std::lock_guard<std::mutex> lk(*db->mu);
-    (*db->variants)[{GPIR_PATH_AUTO, batch}] = best_path;
+    try {
+      (*db->variants)[{GPIR_PATH_AUTO, batch}] = best_path;
+    } catch (...) {
+      return GPIR_ENOMEM;
+    }
   }
   if (variant_out) *variant_out = best_v;
   return GPIR_OK;

@@ -61,7 +61,19 @@ std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, uint32_t>, ntt::Ring> g_r
 
 }  // namespace
 
+static int ring_tables_impl(const gpir_params_t *params, ntt::Ring *out);
+
+// The tables of one parameter set; GPIR_ENOMEM if host memory runs out (no
+// exception leaves this function: it is called from the C ABI).
 int ring_tables(const gpir_params_t *params, ntt::Ring *out) {
+  try {
+    return ring_tables_impl(params, out);
+  } catch (...) {
+    return GPIR_ENOMEM;
+  }
+}
+
+static int ring_tables_impl(const gpir_params_t *params, ntt::Ring *out) {
   const uint32_t N = params->n, L = params->num_limbs;
   if (L < 1 || L > ntt::MAX_LIMBS || N < ntt::MIN_N || N > ntt::MAX_N) return GPIR_ENOTSUP;
   int dev = 0;

@@ -34,6 +34,11 @@ int rowsel_multi_launch(const gpir_job_t *jobs, uint32_t njobs, int path, cudaSt
     // each job on the path gpir_rowsel_batch would take for it (small batches
     // on the CUDA cores); the tensor-core jobs together
     std::vector<gpir_job_t> tc;
+    try {
+      tc.reserve(njobs);   // push_back below then never allocates (no exception crosses the C ABI)
+    } catch (...) {
+      return GPIR_ENOMEM;
+    }
     for (uint32_t k = 0; k < njobs; ++k) {
       const int p = resolve_path(jobs[k].db, GPIR_PATH_AUTO, jobs[k].batch);
       if (p < 0) return GPIR_ENOTSUP;

@@ -38,11 +38,14 @@ bool trace_counters_enabled() {
 
 // Copy a kernel's device counters to the host (synchronizes `s`).
 void trace_counters(const unsigned long long *dev, int n, cudaStream_t s) {
-  std::vector<unsigned long long> h(n, 0);
-  if (cudaMemcpyAsync(h.data(), dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-      cudaStreamSynchronize(s) == cudaSuccess) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_counters = h;
+  try {   // tracing only: an allocation failure drops the counters
+    std::vector<unsigned long long> h(n, 0);
+    if (cudaMemcpyAsync(h.data(), dev, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_counters = h;
+    }
+  } catch (...) {
   }
 }
 
@@ -57,8 +60,14 @@ int trace_begin(const char *name, cudaStream_t s) {
     cudaEventDestroy(r.e0);
     return -1;
   }
+  try {   // tracing only: an allocation failure drops the record
+    g_recs.push_back(r);
+  } catch (...) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+    return -1;
+  }
   cudaEventRecord(r.e0, s);
-  g_recs.push_back(r);
   return (int)g_recs.size() - 1;
 }
 
