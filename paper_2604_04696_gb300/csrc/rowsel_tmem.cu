@@ -252,8 +252,8 @@ __device__ __forceinline__ void tmem_ld4x3(uint32_t t0, uint32_t t1, uint32_t t2
 }
 
 // Ring encoding of a ciphertext residue x < q: the four 7-bit fields of
-// y = centred(x) + O_A, one per byte (bit 7 of bytes 0..2 is don't-care,
-// byte 3 holds y >> 21 <= 128 whole).
+// y = centred(x) + O_A, one per byte (bit 7 of bytes 0..2 clear, byte 3
+// holds y >> 21 <= 128 whole).
 __device__ __forceinline__ uint32_t ct_fields(uint32_t x, uint32_t q, uint32_t h) {
   const uint32_t y = x + kOffA - (x > h ? q : 0u);
   // byte u = field u of y with bit 7 clear (u < 3), byte 3 = y >> 21
@@ -864,7 +864,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       const TmLimb &lm = p.limb[l];
       const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
       const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
-#pragma unroll
+      // column groups c = 0..7 in a loop (not unrolled: a small hot loop for
+      // the instruction caches); the sums rotate so that acc64[0] is c's
+#pragma unroll 1
       for (int c = 0; c < 8; ++c) {
         uint32_t d[12];
         tmem_ld4x3(tbase + c * 4, tbase + 64 + c * 4, tbase + 128 + c * 4, d);
@@ -886,7 +888,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
         }
         const int64_t keep = b1 ? K1[1] : K1[0];
         const int64_t send = b1 ? K1[0] : K1[1];
-        acc64[c] += keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const int64_t a0 = acc64[0] + keep + __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+        for (int k2 = 0; k2 < 7; ++k2) acc64[k2] = acc64[k2 + 1];
+        acc64[7] = a0;   // after the 8 steps acc64[c] is column group c's again
       }
       tc_fence_before();
       __syncwarp();
@@ -1021,11 +1026,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
     uint64_t c = *task_slot;
     uint32_t gbox = 0;
-    // Lane = (k octet j, row parity rp, slot half sh): a warp's 16-byte box
-    // reads at step kk cover all 8 bank groups (4 wavefronts per 512 B, the
-    // minimum) because the thread reads k offset kk ^ (j & 1) and slot half
-    // sh = s4 ^ ((j >> 1) & 1); the byte selectors of the plane transpose
-    // undo the swap of k offsets in odd octets.
+    // Lane = (k octet j, row parity rp, slot half sh). A thread takes the 4
+    // slots of its half one at a time, reading one 4-byte word per k offset:
+    // a loop over the slots keeps the ingest's code small (fully unrolled over
+    // slots, with 16-byte reads, the kernel's hot code outgrew the instruction
+    // caches and ran 2-5% slower). With k offset kk ^ (j & 1) and slot half
+    // sh = (lane & 1) ^ ((j >> 1) & 1) a read instruction touches 8 banks, 4
+    // lanes each (4 wavefronts; 8 without the swaps); the byte selectors of
+    // the plane transpose undo the swap of k offsets in odd octets.
     const int j = lane >> 2, rp = (lane >> 1) & 1;
     const int j0 = j & 1, sh = (lane & 1) ^ ((j >> 1) & 1);
     const uint32_t sel_a = j0 ? 0x1504u : 0x5140u, sel_b = j0 ? 0x3726u : 0x7362u;
@@ -1080,27 +1088,22 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           break;
         }
         if (it == 0) pend &= ~(1u << b);
-        const uint4 *raw4 = reinterpret_cast<const uint4 *>(rawbox + b * Cfg::RAW_BOX);
+        const uint32_t *raw1 = reinterpret_cast<const uint32_t *>(rawbox + b * Cfg::RAW_BOX);
 #pragma unroll 1
         for (int cb = it >> 5; cb < Cfg::BOX_CLIENTS; cb += NT / 32) {
           const int m_local = (part * Cfg::BOX_CLIENTS + cb) * 2 + rp;
-          uint32_t z[8][4];   // [position kk][slot in half]
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint4 v = raw4[((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh];
-            z[kk][0] = ct_fields(v.x, q, h);
-            z[kk][1] = ct_fields(v.y, q, h);
-            z[kk][2] = ct_fields(v.z, q, h);
-            z[kk][3] = ct_fields(v.w, q, h);
-          }
-#pragma unroll
+#pragma unroll 1
           for (int i = 0; i < 4; ++i) {
             const int sl = sh * 4 + i;
             if (t0 + sl >= p.N) continue;
+            uint32_t z[8];   // ring words of k offsets 8j + (kk ^ j0), position kk
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              z[kk] = ct_fields(raw1[(((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh) * 4 + i], q, h);
             uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
             uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
-            digit_planes(z[0][i], z[1][i], z[2][i], z[3][i], sel_a, sel_b, pl);
-            digit_planes(z[4][i], z[5][i], z[6][i], z[7][i], sel_a, sel_b, ph);
+            digit_planes(z[0], z[1], z[2], z[3], sel_a, sel_b, pl);
+            digit_planes(z[4], z[5], z[6], z[7], sel_a, sel_b, ph);
             const uint4 lo = make_uint4(pl[0], ph[0], pl[1], ph[1]);   // chunk 2j: digits 0, 1
             const uint4 hi = make_uint4(pl[2], ph[2], pl[3], ph[3]);   // chunk 2j + 1: digits 2, 3
             if (p.hints) {

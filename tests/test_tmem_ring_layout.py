@@ -2,15 +2,17 @@
 the ingest's byte transpose of encoded residues into digit planes, the
 swizzled 16-byte chunk positions, and the converters' per-digit reads.
 
-The ingest lane (k octet j, row parity, slot half) holds the ring words of its
-octet in position order, position kk carrying k offset kk ^ (j & 1) (the order
-that makes its box reads conflict-free). It transposes them with byte
-permutations into four digit planes, k in order, and stores chunk 2j (digits
-0, 1) and chunk 2j + 1 (digits 2, 3) of its row m at positions c16 ^ (m % 8).
+The ingest lane (k octet j, row parity, slot half) takes the slots of its half
+one at a time and holds the ring words of its octet in position order, position
+kk carrying k offset kk ^ (j & 1) (the order that spreads its 4-byte box reads
+over 8 banks). It transposes them with byte permutations into four digit
+planes, k in order, and stores chunk 2j (digits 0, 1) and chunk 2j + 1 (digits
+2, 3) of its row m at positions c16 ^ (m % 8).
 A converter thread (row m, digit u) reads 8 bytes per octet and builds fp16
 pairs (0x6400 | byte) - 1088. Checked: every converter read returns byte u of
 the row's words in k order, the fp16 pairs equal field - 64, the warp's reads
-are bank-conflict-free, and leaving out the swap of odd octets is caught.
+are bank-conflict-free, the ingest's box reads cover the box once with 4 lanes
+per bank, and leaving out the swap of odd octets is caught.
 """
 
 import numpy as np
@@ -144,3 +146,52 @@ def test_plane_bytes_need_no_mask(u):
         z = ta.ct_fields(x, q)
         b = (z >> np.uint32(8 * u)) & np.uint32(0xFF)
         assert b.max() <= (127 if u < 3 else 128)
+
+
+def box_word(cb, j, kk, rp, sh, i):
+    """Index of the 4-byte box word an ingest thread reads: client cb of the
+    box, k octet j, position kk (k offset kk ^ (j & 1)), row parity rp, slot
+    half sh, slot i of the half. Box layout [client][k][row parity][8 slots]."""
+    return (((cb * 64 + j * 8 + (kk ^ (j & 1))) * 2 + rp) * 2 + sh) * 4 + i
+
+
+def ingest_lane(lane):
+    j, rp = lane >> 2, (lane >> 1) & 1
+    sh = (lane & 1) ^ ((j >> 1) & 1)
+    return j, rp, sh
+
+
+def test_ingest_box_reads_cover_the_box_once():
+    """The 8 warps (one client each) read every word of an 8-client box exactly
+    once: k = 8 j + (kk ^ (j & 1)) runs over 0..63 for each octet."""
+    seen = np.zeros(8 * 64 * 2 * 8, dtype=int)
+    for cb in range(8):
+        for lane in range(32):
+            j, rp, sh = ingest_lane(lane)
+            for i in range(4):
+                for kk in range(8):
+                    seen[box_word(cb, j, kk, rp, sh, i)] += 1
+    assert seen.min() == 1 and seen.max() == 1
+
+
+@pytest.mark.parametrize("swaps", [True, False])
+def test_ingest_box_read_bank_spread(swaps):
+    """Each 4-byte read instruction (fixed kk and i) of a warp touches 8 banks
+    with 4 lanes each; without the k-offset and slot-half swaps it would touch
+    4 banks with 8 lanes each."""
+    for kk in range(8):
+        for i in range(4):
+            banks = np.zeros(32, dtype=int)
+            for lane in range(32):
+                j, rp, sh = ingest_lane(lane)
+                if not swaps:
+                    sh = lane & 1
+                    w = (((0 * 64 + j * 8 + kk) * 2 + rp) * 2 + sh) * 4 + i
+                else:
+                    w = box_word(0, j, kk, rp, sh, i)
+                banks[w % 32] += 1
+            used = banks[banks > 0]
+            if swaps:
+                assert len(used) == 8 and used.max() == 4, (kk, i, banks)
+            else:
+                assert len(used) == 4 and used.max() == 8, (kk, i, banks)
