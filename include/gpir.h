@@ -46,7 +46,7 @@ extern "C" {
 #define GPIR_ECUDA      -4  /* a CUDA runtime call failed                   */
 #define GPIR_ETIMEOUT   -5  /* a bounded wait (host or device) expired      */
 #define GPIR_ENOTSUP    -6  /* path not prepared for this database / device */
-#define GPIR_ETOOBIG    -7  /* problem needs more than a fixed-size buffer  */
+#define GPIR_ETOOBIG    -7  /* problem exceeds a fixed buffer or index size */
 
 /* ---- compute paths (also usable as a bit mask at upload) ---------------- */
 #define GPIR_PATH_AUTO      0  /* fastest prepared path for the shape        */
@@ -110,7 +110,9 @@ size_t gpir_db_device_bytes(const gpir_db_t *db);
  * precondition, checked only with the debug checks on (gpir_set_debug),
  * because a check adds a pass over the ciphertext stream. Results are
  * canonical and identical for every path.
- * GPIR_ENOTSUP if `path` was not prepared at upload. The tensor-core path
+ * GPIR_ENOTSUP if `path` was not prepared at upload; GPIR_ETOOBIG if a
+ * tensor-core launch would number 2^32 or more work units (never for inputs
+ * that fit in device memory). The tensor-core path
  * keeps its per-batch digit tiles (2x the ciphertext bytes) in a workspace
  * owned by the library per (device, stream), grown on demand; calls on
  * different streams may overlap. Asynchronous. */

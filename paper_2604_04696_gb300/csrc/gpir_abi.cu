@@ -298,7 +298,7 @@ const char *gpir_strerror(int code) {
     case GPIR_ECUDA: return "CUDA runtime error";
     case GPIR_ETIMEOUT: return "bounded wait expired";
     case GPIR_ENOTSUP: return "path not prepared or not supported";
-    case GPIR_ETOOBIG: return "problem exceeds the fixed-size workspace";
+    case GPIR_ETOOBIG: return "problem exceeds a fixed-size workspace or the kernel index range";
   }
   return "unknown gpir error";
 }

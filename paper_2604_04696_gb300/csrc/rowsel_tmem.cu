@@ -515,8 +515,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   // global entry of a unit for this CTA
   auto entry_of = [&](uint64_t u) -> uint64_t {
     const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
-    const uint64_t ul = u - jb.unit0;
-    return jb.entry0 + (PAIR ? (ul / jb.upe) * 2 + rank : ul / jb.upe);
+    const uint32_t ul = (uint32_t)(u - jb.unit0);
+    return jb.entry0 + (PAIR ? (uint64_t)(ul / jb.upe) * 2 + rank : (uint64_t)(ul / jb.upe));
   };
   // index of the first unit that reads entry e
   auto first_unit_of = [&](uint64_t e) -> uint64_t {
@@ -584,10 +584,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       while (ok && u != kNoUnit) {
         const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
         const uint64_t E = entry_of(u);
-        const uint32_t w = (uint32_t)((u - jb.unit0) % jb.upe), sl = w / jb.nblk, nb = w % jb.nblk;
-        const uint32_t g = (uint32_t)((E - jb.entry0) / jb.mblk);
+        const uint32_t w = (uint32_t)(u - jb.unit0) % jb.upe, sl = w / jb.nblk, nb = w % jb.nblk;
+        const uint32_t g = (uint32_t)(E - jb.entry0) / jb.mblk;
         const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        const uint8_t *src_a = p.ring + (((E % p.R) * 8 + sl) * p.kch_max) * (uint64_t)T_RAW_TILE;
+        const uint8_t *src_a = p.ring + (((uint64_t)((uint32_t)E % p.R) * 8 + sl) * p.kch_max) * (uint64_t)T_RAW_TILE;
         const uint8_t *src_b = (const uint8_t *)jb.b_tiles + ((slot * jb.nblk + nb) * jb.kch) * (uint64_t)T_B_TILE +
                                (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
         const uint32_t kch = jb.kch;
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       const uint64_t un = tag & ~(1ull << 63);
       const bool last = (tag >> 63) != 0;
       const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
-      const uint32_t l = (uint32_t)((entry_of(un) - jb.entry0) / jb.mblk) / p.gpl;
+      const uint32_t l = ((uint32_t)(entry_of(un) - jb.entry0) / jb.mblk) / p.gpl;
       const TmLimb &lm = p.limb[l];
       const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
       const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
@@ -958,8 +958,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       if (un == kNoUnit) break;
       const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
       const uint64_t El = entry_of(un) - jb.entry0;
-      const uint32_t w = (uint32_t)((un - jb.unit0) % jb.upe), sl = w / jb.nblk, nb = w % jb.nblk;
-      const uint32_t g = (uint32_t)(El / jb.mblk), mb = (uint32_t)(El % jb.mblk);
+      const uint32_t w = (uint32_t)(un - jb.unit0) % jb.upe, sl = w / jb.nblk, nb = w % jb.nblk;
+      const uint32_t g = (uint32_t)El / jb.mblk, mb = (uint32_t)El % jb.mblk;
       const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
       const uint32_t mrows = min((uint32_t)T_MROWS, jb.M - mb * T_MROWS);
       const uint32_t ncols = min((uint32_t)T_NCOLS, jb.d1 - nb * T_NCOLS);
@@ -998,9 +998,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     auto issue = [&](uint32_t gb, uint64_t task, int part) {
       // box gb (global box index) of `task`, part `part`, into buffer gb % 2
       const TmJob &jb = p.job[job_of_task<MULTI>(p, task)];
-      const uint64_t tl = task - jb.task0, El = tl / jb.kch;
-      const uint32_t kc = (uint32_t)(tl % jb.kch);
-      const uint32_t g = (uint32_t)(El / jb.mblk), mb = (uint32_t)(El % jb.mblk);
+      const uint32_t tl = (uint32_t)(task - jb.task0), El = tl / jb.kch;
+      const uint32_t kc = tl % jb.kch;
+      const uint32_t g = El / jb.mblk, mb = El % jb.mblk;
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       const uint32_t b = gb & 1u;
       const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
@@ -1040,10 +1040,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
     while (c != kNoUnit) {
       const TmJob &jb = p.job[job_of_task<MULTI>(p, c)];
-      const uint64_t tl = c - jb.task0, El = tl / jb.kch;
+      const uint32_t tl = (uint32_t)(c - jb.task0), El = tl / jb.kch;
       const uint64_t E = jb.entry0 + El;   // global entry
-      const uint32_t kc = (uint32_t)(tl % jb.kch);
-      const uint32_t g = (uint32_t)(El / jb.mblk);
+      const uint32_t kc = tl % jb.kch;
+      const uint32_t g = El / jb.mblk;
       const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
       if (it == 0) {
         // ring slot E % R: its previous entry E - R read by all of its units;
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
               z[kk] = ct_fields(raw1[(((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh) * 4 + i], q, h);
-            uint4 *tile = ring4 + ((((E % p.R) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
+            uint4 *tile = ring4 + ((((uint64_t)((uint32_t)E % p.R) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
             uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
             digit_planes(z[0], z[1], z[2], z[3], sel_a, sel_b, pl);
             digit_planes(z[4], z[5], z[6], z[7], sel_a, sel_b, ph);
@@ -1319,6 +1319,10 @@ int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_targ
     const int rc = encode_tiled_u32(&jb.ct_map, jobs[k].ct, 5, dims, str, box);
     if (rc != GPIR_OK) return rc;
   }
+  // The kernel divides unit, entry and ingest-task indices in 32 bits. Any
+  // launch whose ciphertexts fit in device memory has far fewer than 2^32 of
+  // each (an entry alone covers 16 clients' 8 slots of every row).
+  if (units > UINT32_MAX || entries > UINT32_MAX || tasks > UINT32_MAX) return GPIR_ETOOBIG;
   tp.n_entries = entries;
   tp.n_units = units;
   tp.n_tasks = tasks;
