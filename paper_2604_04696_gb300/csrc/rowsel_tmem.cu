@@ -129,12 +129,26 @@ struct TmLimb {
   int32_t w[4][3];       // 2^(7u + 10v) mod q
 };
 
+// Division of a 32-bit index by a launch constant d >= 1 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// with l = ceil(log2 d) and the 33-bit multiplier 2^32 + m,
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l for
+// every n < 2^32. Written on the host by tm_div.
+struct TmDiv {
+  uint32_t d, m, l;
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    return (uint32_t)(((uint64_t)__umulhi(n, m) + n) >> l);
+  }
+  __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
+
 // One RowSel problem of a launch. Its entries, units and ingest tasks are
 // numbered after those of the jobs before it, in one index space per launch.
 constexpr int T_MAX_JOBS = 8;
 struct TmJob {
   CUtensorMap ct_map;                   // box (8 slots, 1, 2, 64 k, BOX_CLIENTS clients)
   uint32_t M, d1, mblk, nblk, kch, upe;
+  TmDiv mblk_d, nblk_d, kch_d, upe_d;   // the same four as divisors
   uint64_t entry0, unit0, task0;        // first entry / unit / ingest task of the job
   const uint16_t *b_tiles;              // [slot][nblk][kch] x 24 KB
   uint32_t *out;
@@ -144,6 +158,7 @@ struct TmemParams {
   TmJob job[T_MAX_JOBS];
   uint32_t L, N, njobs, kch_max;
   uint32_t R, gpl, spg, lookahead;
+  TmDiv R_d, gpl_d;
   uint32_t hints;                       // 1: raw boxes evict-first, ring stores evict-last in L2
   uint64_t n_entries, n_units, n_tasks; // over all jobs
   uint8_t *ring;                        // [R][8 slots][kch_max] x 8 KB
@@ -516,7 +531,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
   auto entry_of = [&](uint64_t u) -> uint64_t {
     const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
     const uint32_t ul = (uint32_t)(u - jb.unit0);
-    return jb.entry0 + (PAIR ? (uint64_t)(ul / jb.upe) * 2 + rank : (uint64_t)(ul / jb.upe));
+    return jb.entry0 + (PAIR ? (uint64_t)jb.upe_d.div(ul) * 2 + rank : (uint64_t)jb.upe_d.div(ul));
   };
   // index of the first unit that reads entry e
   auto first_unit_of = [&](uint64_t e) -> uint64_t {
@@ -584,10 +599,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       while (ok && u != kNoUnit) {
         const TmJob &jb = p.job[job_of_unit<MULTI>(p, u)];
         const uint64_t E = entry_of(u);
-        const uint32_t w = (uint32_t)(u - jb.unit0) % jb.upe, sl = w / jb.nblk, nb = w % jb.nblk;
-        const uint32_t g = (uint32_t)(E - jb.entry0) / jb.mblk;
-        const uint64_t slot = (uint64_t)(g / p.gpl) * p.N + (g % p.gpl) * 8 + sl;
-        const uint8_t *src_a = p.ring + (((uint64_t)((uint32_t)E % p.R) * 8 + sl) * p.kch_max) * (uint64_t)T_RAW_TILE;
+        const uint32_t w = jb.upe_d.mod((uint32_t)(u - jb.unit0)), sl = jb.nblk_d.div(w), nb = w - sl * jb.nblk;
+        const uint32_t g = jb.mblk_d.div((uint32_t)(E - jb.entry0));
+        const uint32_t gl = p.gpl_d.div(g);
+        const uint64_t slot = (uint64_t)gl * p.N + (g - gl * p.gpl) * 8 + sl;
+        const uint8_t *src_a = p.ring + (((uint64_t)p.R_d.mod((uint32_t)E) * 8 + sl) * p.kch_max) * (uint64_t)T_RAW_TILE;
         const uint8_t *src_b = (const uint8_t *)jb.b_tiles + ((slot * jb.nblk + nb) * jb.kch) * (uint64_t)T_B_TILE +
                                (PAIR ? rank * (uint64_t)Cfg::B_BYTES : 0ull);
         const uint32_t kch = jb.kch;
@@ -860,7 +876,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       const uint64_t un = tag & ~(1ull << 63);
       const bool last = (tag >> 63) != 0;
       const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
-      const uint32_t l = ((uint32_t)(entry_of(un) - jb.entry0) / jb.mblk) / p.gpl;
+      const uint32_t l = p.gpl_d.div(jb.mblk_d.div((uint32_t)(entry_of(un) - jb.entry0)));
       const TmLimb &lm = p.limb[l];
       const int32_t w0 = lm.w[u][0], w1 = lm.w[u][1], w2 = lm.w[u][2];
       const uint32_t tbase = tmem_base + ((qw * 32u) << 16) + buf * T_ACC_COLS + half * 32u;
@@ -958,9 +974,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
       if (un == kNoUnit) break;
       const TmJob &jb = p.job[job_of_unit<MULTI>(p, un)];
       const uint64_t El = entry_of(un) - jb.entry0;
-      const uint32_t w = (uint32_t)(un - jb.unit0) % jb.upe, sl = w / jb.nblk, nb = w % jb.nblk;
-      const uint32_t g = (uint32_t)El / jb.mblk, mb = (uint32_t)El % jb.mblk;
-      const uint32_t l = g / p.gpl, t = (g % p.gpl) * 8 + sl;
+      const uint32_t w = jb.upe_d.mod((uint32_t)(un - jb.unit0)), sl = jb.nblk_d.div(w), nb = w - sl * jb.nblk;
+      const uint32_t g = jb.mblk_d.div((uint32_t)El), mb = (uint32_t)El - g * jb.mblk;
+      const uint32_t l = p.gpl_d.div(g), t = (g - l * p.gpl) * 8 + sl;
       const uint32_t mrows = min((uint32_t)T_MROWS, jb.M - mb * T_MROWS);
       const uint32_t ncols = min((uint32_t)T_NCOLS, jb.d1 - nb * T_NCOLS);
       const uint64_t nstride = (uint64_t)2 * p.L * p.N;
@@ -998,10 +1014,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     auto issue = [&](uint32_t gb, uint64_t task, int part) {
       // box gb (global box index) of `task`, part `part`, into buffer gb % 2
       const TmJob &jb = p.job[job_of_task<MULTI>(p, task)];
-      const uint32_t tl = (uint32_t)(task - jb.task0), El = tl / jb.kch;
-      const uint32_t kc = tl % jb.kch;
-      const uint32_t g = El / jb.mblk, mb = El % jb.mblk;
-      const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
+      const uint32_t tl = (uint32_t)(task - jb.task0), El = jb.kch_d.div(tl);
+      const uint32_t kc = tl - El * jb.kch;
+      const uint32_t g = jb.mblk_d.div(El), mb = El - g * jb.mblk;
+      const uint32_t l = p.gpl_d.div(g), t0 = (g - l * p.gpl) * 8;
       const uint32_t b = gb & 1u;
       const int c0 = (int)(mb * T_TASK_CLIENTS) + part * Cfg::BOX_CLIENTS;
       uint8_t *dst = rawbox + b * Cfg::RAW_BOX;
@@ -1040,11 +1056,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
     uint4 *ring4 = reinterpret_cast<uint4 *>(p.ring);
     while (c != kNoUnit) {
       const TmJob &jb = p.job[job_of_task<MULTI>(p, c)];
-      const uint32_t tl = (uint32_t)(c - jb.task0), El = tl / jb.kch;
+      const uint32_t tl = (uint32_t)(c - jb.task0), El = jb.kch_d.div(tl);
       const uint64_t E = jb.entry0 + El;   // global entry
-      const uint32_t kc = tl % jb.kch;
-      const uint32_t g = El / jb.mblk;
-      const uint32_t l = g / p.gpl, t0 = (g % p.gpl) * 8;
+      const uint32_t kc = tl - El * jb.kch;
+      const uint32_t g = jb.mblk_d.div(El);
+      const uint32_t l = p.gpl_d.div(g), t0 = (g - l * p.gpl) * 8;
       if (it == 0) {
         // ring slot E % R: its previous entry E - R read by all of its units;
         // and at most `lookahead` entries ahead of the units claimed
@@ -1100,7 +1116,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
               z[kk] = ct_fields(raw1[(((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh) * 4 + i], q, h);
-            uint4 *tile = ring4 + ((((uint64_t)((uint32_t)E % p.R) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
+            uint4 *tile = ring4 + ((((uint64_t)p.R_d.mod((uint32_t)E) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
             uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
             digit_planes(z[0], z[1], z[2], z[3], sel_a, sel_b, pl);
             digit_planes(z[4], z[5], z[6], z[7], sel_a, sel_b, ph);
@@ -1283,6 +1299,15 @@ int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_targ
   if (pair && g_tm_pairs[dev] < 0) return GPIR_ENOTSUP;
   const gpir_params &prm = jobs[0].db->params;
   const uint32_t L = prm.num_limbs, N = prm.n;
+  auto tm_div = [](uint32_t d) {
+    TmDiv v;
+    if (d == 0) d = 1;   // not reached: every divisor counts at least one item
+    v.d = d;
+    v.l = 0;
+    while ((1ull << v.l) < d) ++v.l;
+    v.m = (uint32_t)((((uint64_t)1 << 32) * ((1ull << v.l) - d)) / d + 1);
+    return v;
+  };
   TmemParams tp;
   memset(&tp, 0, sizeof(tp));
   tp.L = L;
@@ -1301,6 +1326,10 @@ int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_targ
     jb.nblk = (db->d1 + T_NCOLS - 1) / T_NCOLS;
     jb.kch = (db->d0 + T_KCHUNK - 1) / T_KCHUNK;
     jb.upe = tp.spg * jb.nblk;
+    jb.mblk_d = tm_div(jb.mblk);
+    jb.nblk_d = tm_div(jb.nblk);
+    jb.kch_d = tm_div(jb.kch);
+    jb.upe_d = tm_div(jb.upe);
     jb.entry0 = entries;
     jb.unit0 = units;
     jb.task0 = tasks;
@@ -1333,6 +1362,8 @@ int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_targ
   if (pair && (R & 1)) ++R;   // both entries of a pair unit share R's parity classes
   if (R > tp.n_entries) R = tp.n_entries;
   tp.R = (uint32_t)R;
+  tp.R_d = tm_div(tp.R);
+  tp.gpl_d = tm_div(tp.gpl);
   const size_t ring_bytes = (size_t)R * entry_bytes;
   // counters: [2] claims, ready[n_entries], consumed[n_entries], role counters
   const size_t flag_bytes = ((size_t)16 + 8 * entries + 8 + 8 * kNumTmemCounters + 255) & ~(size_t)255;
