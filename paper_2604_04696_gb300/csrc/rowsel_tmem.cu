@@ -270,12 +270,12 @@ __device__ __forceinline__ void tmem_ld4x3(uint32_t t0, uint32_t t1, uint32_t t2
 // y = centred(x) + O_A, one per byte (bit 7 of bytes 0..2 clear, byte 3
 // holds y >> 21 <= 128 whole).
 __device__ __forceinline__ uint32_t ct_fields(uint32_t x, uint32_t q, uint32_t h) {
-  const uint32_t y = x + kOffA - (x > h ? q : 0u);
-  // byte u = field u of y with bit 7 clear (u < 3), byte 3 = y >> 21
-  uint32_t z = (y & 0x7Fu) | ((y << 1) & 0xFFFFFF00u);
-  z = (z & 0x7FFFu) | ((y << 2) & 0xFFFF0000u);
-  z = (z & 0x7FFFFFu) | ((y << 3) & 0xFF000000u);
-  return z;
+  const uint32_t y = x + kOffA - (x > h ? q : 0u);   // < 2^29
+  // byte u = field u of y with bit 7 clear (u < 3), byte 3 = y >> 21, by two
+  // spreads done as adds: bits 14.. of y up by 2 (a = y + 3 (y & ~0x3FFF)),
+  // then bits 7..13 and 21.. of each 16-bit half up by 1
+  const uint32_t a = y + 3u * (y & 0xFFFFC000u);
+  return a + (a & 0x7F807F80u);
 }
 
 // Ring tile row (256 bytes, one ciphertext row of a k-chunk): 16-byte chunk
@@ -1112,10 +1112,15 @@ __global__ void __launch_bounds__(T_THREADS, 1) tc_tmem_kernel(const __grid_cons
           for (int i = 0; i < 4; ++i) {
             const int sl = sh * 4 + i;
             if (t0 + sl >= p.N) continue;
-            uint32_t z[8];   // ring words of k offsets 8j + (kk ^ j0), position kk
+            // ring words of k offsets 8j + (kk ^ j0), position kk: box word
+            // ((cb * 64 + k) * 2 + rp) * 8 + sh * 4 + i, from one base for the
+            // even positions and one for the odd (k offset kk + j0 / kk - j0)
+            uint32_t z[8];
+            const uint32_t *be = raw1 + ((cb * T_KCHUNK + j * 8) * 2 + rp) * 8 + sh * 4 + i + j0 * 16;
+            const uint32_t *bo = be - 2 * j0 * 16;
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk)
-              z[kk] = ct_fields(raw1[(((cb * T_KCHUNK + j * 8 + (kk ^ j0)) * 2 + rp) * 2 + sh) * 4 + i], q, h);
+              z[kk] = ct_fields((kk & 1) ? bo[kk * 16] : be[kk * 16], q, h);
             uint4 *tile = ring4 + ((((uint64_t)p.R_d.mod((uint32_t)E) * 8 + sl) * p.kch_max + kc) * (uint64_t)T_RAW_TILE) / 16;
             uint32_t pl[4], ph[4];   // digit planes of k 8j .. 8j + 3 and 8j + 4 .. 8j + 7
             digit_planes(z[0], z[1], z[2], z[3], sel_a, sel_b, pl);

@@ -338,14 +338,29 @@ FLUSH12 = 4
 
 def ct_fields(x, q):
     """The ring encoding z of ciphertext residues x (uint32 array), bit for bit
-    as the kernel's shift-and-merge sequence computes it."""
+    as the kernel computes it: y = centred(x) + O_A, a = y + 3 (y & ~0x3FFF)
+    (bits 14.. up by 2), z = a + (a & 0x7F807F80) (bits 7..13 and 21.. of each
+    16-bit half up by 1), in 32-bit arithmetic."""
     x = np.asarray(x, dtype=np.uint32)
     h = np.uint32((q - 1) // 2)
     y = (x + np.uint32(O_A) - np.where(x > h, np.uint32(q), np.uint32(0))).astype(np.uint32)
-    z = (y & np.uint32(0x7F)) | ((y << np.uint32(1)) & np.uint32(0xFFFFFF00))
-    z = (z & np.uint32(0x7FFF)) | ((y << np.uint32(2)) & np.uint32(0xFFFF0000))
-    z = (z & np.uint32(0x7FFFFF)) | ((y << np.uint32(3)) & np.uint32(0xFF000000))
-    return z
+    a = (y + np.uint32(3) * (y & np.uint32(0xFFFFC000))).astype(np.uint32)
+    return (a + (a & np.uint32(0x7F807F80))).astype(np.uint32)
+
+
+def test_ring_encoding_is_the_field_split():
+    """The add-based spreads give byte u = field u of y (7 bits, u < 3) and
+    byte 3 = y >> 21, as the shift-and-mask definition does, for every residue
+    of each prime's edge cases and a random sample."""
+    rng = np.random.default_rng(23)
+    for q in list(PRIMES) + [17, 97, 268042241]:
+        h = (q - 1) // 2
+        x = np.concatenate([rng.integers(0, q, 50000), [0, 1, h, h + 1, q - 1, q - 2]]).astype(np.int64)
+        x = x[x < q]
+        y = x + O_A - np.where(x > h, q, 0)
+        assert y.min() >= 0 and y.max() < (1 << 29)
+        want = (y & 0x7F) | (((y >> 7) & 0x7F) << 8) | (((y >> 14) & 0x7F) << 16) | ((y >> 21) << 24)
+        assert np.array_equal(ct_fields(x.astype(np.uint32), q).astype(np.int64), want)
 
 
 def ct_digit_fp16(z, u):
