@@ -1955,9 +1955,9 @@ constexpr FusedVariant kFusedVariants[] = {
     {kKindFused, 40, kHintRing, 16},    // 5
     {kKindCluster, 0, 0, 0},            // 6: 8-CTA clusters sharing raw boxes over DSMEM
     {kKindPair, 48, 0, 16},             // 7: SM pairs (cta_group::2) sharing each database tile
-    {kKindTmem, 48, 0, 16},             // 8: A operand in tensor memory, 12 digit products
+    {kKindTmem, 24, 0, 8},              // 8: A operand in tensor memory, 12 digit products
     {kKindTmemPair, 48, 0, 16},         // 9: its SM-pair form
-    {kKindTmem, 48, 1, 16},             // 10: 8 with raw boxes evict-first, ring stores evict-last
+    {kKindTmem, 24, 1, 8},              // 10: 8 with raw boxes evict-first, ring stores evict-last
     {kKindTmemPair, 48, 1, 16},         // 11: 9 with those hints
 };
 constexpr int kNumTcVariants = (int)(sizeof(kFusedVariants) / sizeof(kFusedVariants[0]));

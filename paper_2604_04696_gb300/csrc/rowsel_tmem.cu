@@ -104,8 +104,8 @@ struct TmemCfg {
   static constexpr int NBUF = 4 / KPB;                              // A buffers (128 columns)
   static constexpr int BOX_CLIENTS = 8;                             // clients per ingest box (two buffers)
   static constexpr int RAW_BOX = BOX_CLIENTS * T_KCHUNK * 2 * 8 * 4;   // x 64 k x 2 x 8 slots x 4 B
-  static constexpr int NS = PAIR ? 8 : 4;                           // B stages
-  static constexpr int RS = 6;                                      // ring slots
+  static constexpr int NS = PAIR ? 8 : 5;                           // B stages
+  static constexpr int RS = PAIR ? 6 : 4;                           // ring slots
   static constexpr size_t SMEM =
       1024 + (size_t)NS * B_BYTES + (size_t)RS * T_RAW_TILE + 2 * (size_t)RAW_BOX + T_OUT_BYTES + 1024;
   static_assert(KPB == 1 || KPB == 2, "an A buffer holds one k-chunk or one of each converter set");
@@ -1421,7 +1421,7 @@ int tc_launch_tmem_jobs(const gpir_job_t *jobs, uint32_t njobs, size_t ring_targ
 int rowsel_tmem_multi(const gpir_job_t *jobs, uint32_t njobs, cudaStream_t stream) {
   for (uint32_t k0 = 0; k0 < njobs; k0 += T_MAX_JOBS) {
     const uint32_t n = std::min<uint32_t>(T_MAX_JOBS, njobs - k0);
-    const int rc = tc_launch_tmem_jobs(jobs + k0, n, (size_t)48 << 20, 16, 0, false, stream);
+    const int rc = tc_launch_tmem_jobs(jobs + k0, n, (size_t)24 << 20, 8, 0, false, stream);
     if (rc != GPIR_OK) return rc;
   }
   return GPIR_OK;

@@ -348,7 +348,7 @@ def run_model(pair, ns, n_units, kch, kgroup, seed, skip_aempty=False, kpb=1, af
     return True
 
 
-@pytest.mark.parametrize("pair,ns,rs", [(False, 4, 6), (True, 8, 8), (True, 4, 6), (False, 6, 4), (True, 6, 10)])
+@pytest.mark.parametrize("pair,ns,rs", [(False, 5, 4), (False, 4, 6), (True, 8, 6), (True, 4, 6), (False, 6, 4), (True, 6, 10)])
 @pytest.mark.parametrize("n_units,kch", [(0, 3), (1, 3), (5, 3), (3, 16), (7, 9)])
 @pytest.mark.parametrize("kpb", [1, 2])
 def test_protocol_random_interleavings(pair, ns, rs, n_units, kch, kpb):
