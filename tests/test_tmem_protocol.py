@@ -448,3 +448,31 @@ def test_converter_skipping_the_b_stage_wait_is_caught(pair):
         except AssertionError:
             bad += 1
     assert bad > 0
+
+
+def _kernel_cfg():
+    """(NS, RS, KPB) of both forms, read from the kernel source's TmemCfg."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2604_04696_gb300", "csrc", "rowsel_tmem.cu"), encoding="utf-8").read()
+
+    def value(name, pair):
+        m = re.search(r"static constexpr int %s = ([^;]+);" % name, src)
+        assert m, name
+        e = m.group(1).strip()
+        t = re.fullmatch(r"PAIR \? (\d+) : (\d+)", e)
+        return int(t.group(1) if pair else t.group(2)) if t else int(e)
+
+    return {pair: (value("NS", pair), value("RS", pair), value("KPB", pair)) for pair in (False, True)}
+
+
+@pytest.mark.parametrize("pair", [False, True])
+@pytest.mark.parametrize("n_units,kch", [(1, 1), (6, 3), (4, 16), (9, 5)])
+def test_protocol_with_the_kernels_own_configuration(pair, n_units, kch):
+    """The stage, ring-slot and A-buffer counts the kernel is compiled with
+    (read from its source) run the protocol without deadlock or stale reads."""
+    ns, rs, kpb = _kernel_cfg()[pair]
+    assert rs % 2 == 0 and ns >= 4
+    for seed in range(20):
+        run_model(pair, ns, n_units, kch, 8, seed, kpb=kpb, rs=rs)
